@@ -1,0 +1,190 @@
+"""CPU oracle of the hybrid denoiser (adaptive median -> local-statistics Wiener).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / reference leg are the only callers.  The CUDA
+library never imports this package and shares no code with it.
+
+The arithmetic lives in ``hd_oracle.c`` (plain C, compiled with gcc, binary64
+unless stated); this module compiles it on first use and wraps it with numpy.
+What each function follows in the paper:
+
+* ``amf``          - Algorithm 1, step 6 (adaptive median, level A / level B,
+                     window growth k = 3..Smax over the noisy image).
+* ``wiener``       - Algorithm 1, step 4d, in the spatial local-statistics
+                     form (local mean / variance over w x w, noise variance =
+                     mean local variance unless supplied).
+* ``hybrid``       - Algorithm 1, step 4: Wiener(AMF(g)).  The contrast
+                     stretch of step 4e is not part of this path.
+
+Pins: every function here is checked, in ``tests/test_oracle_pins.py``,
+against brute force on tiny images, library order-statistic filters,
+closed forms and exact rational arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hd_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORACLE_OK = 0
+ORACLE_ERR_ARG = 1
+ORACLE_ERR_SMAX = 2
+ORACLE_ERR_WINDOW = 3
+ORACLE_ERR_OOM = 5
+
+
+def build(force: bool = False) -> str:
+    """Compile hd_oracle.c into liboracle.so next to it (gcc, -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["cc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            L = ctypes.c_long
+            I = ctypes.c_int
+            lib.oracle_amf.argtypes = [P, P, L, L, I, I, P]
+            lib.oracle_amf.restype = I
+            lib.oracle_wiener.argtypes = [P, L, L, I, I, ctypes.c_double, I, P, P, P, P, P, P]
+            lib.oracle_wiener.restype = I
+            lib.oracle_wiener_stats.argtypes = [P, L, L, I, I, P, P]
+            lib.oracle_wiener_stats.restype = I
+            lib.oracle_amf_pixel.argtypes = [P, L, L, I, I, L, L]
+            lib.oracle_amf_pixel.restype = I
+            lib.oracle_check_smax.argtypes = [I]
+            lib.oracle_check_smax.restype = I
+            _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: oracle status {code}")
+        self.code = code
+
+
+def _as_u16(img: np.ndarray) -> np.ndarray:
+    if img.ndim != 2:
+        raise ValueError("image must be 2-D")
+    if img.dtype not in (np.uint8, np.uint16):
+        raise TypeError("image must be uint8 or uint16")
+    return np.ascontiguousarray(img, dtype=np.uint16)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def check_smax(smax: int) -> int:
+    """Algorithm 1, step 6a: status 0 if Smax is an odd integer > 1, else 2."""
+    return _load().oracle_check_smax(int(smax))
+
+
+def amf(g: np.ndarray, smax: int, keep_unresolved: bool = False, return_k: bool = False):
+    """Adaptive median filter of the noisy image ``g`` (Algorithm 1, step 6).
+
+    Returns the filtered image with ``g``'s dtype (and, with ``return_k``, the
+    window size at which each pixel passed level A, 0 where none did).
+    """
+    lib = _load()
+    g16 = _as_u16(g)
+    H, W = g16.shape
+    f = np.empty_like(g16)
+    kk = np.empty((H, W), dtype=np.uint8) if return_k else None
+    rc = lib.oracle_amf(_ptr(g16), _ptr(f), H, W, int(smax), int(bool(keep_unresolved)), _ptr(kk))
+    if rc != ORACLE_OK:
+        raise OracleError(rc, "oracle_amf")
+    out = f.astype(g.dtype)
+    return (out, kk) if return_k else out
+
+
+def amf_pixel(g: np.ndarray, smax: int, y: int, x: int, keep_unresolved: bool = False) -> int:
+    """Adaptive median of one pixel (for sampled checks of large images)."""
+    lib = _load()
+    g16 = g if (g.dtype == np.uint16 and g.flags.c_contiguous) else _as_u16(g)
+    H, W = g16.shape
+    v = lib.oracle_amf_pixel(_ptr(g16), H, W, int(smax), int(bool(keep_unresolved)), int(y), int(x))
+    if v < 0:
+        raise OracleError(ORACLE_ERR_ARG, "oracle_amf_pixel")
+    return v
+
+
+@dataclass
+class WienerResult:
+    out64: np.ndarray      # round-half-up of y64, input dtype
+    y64: np.ndarray        # binary64 value (the paper's precision)
+    out32: np.ndarray      # rounding of the binary32 twin, input dtype
+    y32: np.ndarray        # binary32 twin in the kernel's evaluation order
+    nu2: float             # noise variance used
+    sumD: int              # exact sum over pixels of D = n*S2 - S1^2
+
+
+def wiener(f: np.ndarray, w: int, noise_var: float = -1.0, bits: int | None = None,
+           border_zero: bool = False) -> WienerResult:
+    """Local-statistics Wiener filter of the integer image ``f``.
+
+    ``noise_var < 0`` estimates the noise variance as the mean local variance.
+    ``bits`` sets the output clamp 2^bits - 1 (default: 8 for uint8, 16 for uint16).
+    """
+    lib = _load()
+    f16 = _as_u16(f)
+    H, W = f16.shape
+    if bits is None:
+        bits = 8 if f.dtype == np.uint8 else 16
+    maxv = (1 << int(bits)) - 1
+    out64 = np.empty_like(f16)
+    out32 = np.empty_like(f16)
+    y64 = np.empty((H, W), dtype=np.float64)
+    y32 = np.empty((H, W), dtype=np.float32)
+    nu2 = ctypes.c_double()
+    sumD = np.zeros(2, dtype=np.uint64)
+    rc = lib.oracle_wiener(_ptr(f16), H, W, int(w), int(bool(border_zero)), float(noise_var), maxv,
+                           _ptr(out64), _ptr(y64), _ptr(out32), _ptr(y32),
+                           ctypes.byref(nu2), _ptr(sumD))
+    if rc != ORACLE_OK:
+        raise OracleError(rc, "oracle_wiener")
+    total = int(sumD[0]) + (int(sumD[1]) << 64)
+    return WienerResult(out64.astype(f.dtype), y64, out32.astype(f.dtype), y32, nu2.value, total)
+
+
+def wiener_stats(f: np.ndarray, w: int, border_zero: bool = False):
+    """(S1, D) per pixel as uint64 arrays, D = n*S2 - S1^2."""
+    lib = _load()
+    f16 = _as_u16(f)
+    H, W = f16.shape
+    S1 = np.empty((H, W), dtype=np.uint64)
+    D = np.empty((H, W), dtype=np.uint64)
+    rc = lib.oracle_wiener_stats(_ptr(f16), H, W, int(w), int(bool(border_zero)), _ptr(S1), _ptr(D))
+    if rc != ORACLE_OK:
+        raise OracleError(rc, "oracle_wiener_stats")
+    return S1, D
+
+
+def hybrid(g: np.ndarray, smax: int, w: int, noise_var: float = -1.0, bits: int | None = None,
+           keep_unresolved: bool = False, border_zero: bool = False):
+    """Algorithm 1, step 4 without the contrast stretch: Wiener(AMF(g)).
+
+    Returns (f, WienerResult) where f is the adaptive-median output.
+    """
+    f = amf(g, smax, keep_unresolved=keep_unresolved)
+    return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero)

@@ -1,0 +1,307 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Adaptive median (Algorithm 1, step 6):
+  * hand-derived worked examples (tests/golden/amf_worked_examples.json),
+  * exhaustive brute force on every binary 3x3 image and random tiny images,
+  * reduction to library order-statistic filters (scipy.ndimage, mode
+    "reflect" = half-sample symmetric) for every window size,
+  * invariants: constant image, isolated impulses, output range.
+Wiener (Algorithm 1, step 4d, local-statistics form):
+  * exact rational arithmetic (two-pass variance) on small images,
+  * closed forms: constant, checkerboard c +- d, linear ramp,
+  * limits: nu2 = 0 gives the identity, huge nu2 gives the box mean,
+  * library routine scipy.signal.wiener with zero borders,
+  * the binary32 twin within maxv * 2^-20 of binary64.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._brute import amf_brute, local_stats_exact, wiener_exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "amf_worked_examples.json")
+
+
+# --------------------------------------------------------------------------- AMF
+def test_smax_validation():
+    # Algorithm 1, step 6a: Smax must be an odd integer > 1.
+    for bad in (-3, 0, 1, 2, 4, 10, 12):
+        assert oracle.check_smax(bad) == oracle.ORACLE_ERR_SMAX
+        with pytest.raises(oracle.OracleError):
+            oracle.amf(np.zeros((4, 4), np.uint8), bad)
+    for good in (3, 5, 7, 9, 11, 15):
+        assert oracle.check_smax(good) == oracle.ORACLE_OK
+
+
+def test_amf_golden_worked_examples():
+    cases = json.load(open(GOLDEN))["cases"]
+    for c in cases:
+        g = np.array(c["image"], dtype=np.uint8)
+        f = oracle.amf(g, c["smax"])
+        if "expected" in c:
+            np.testing.assert_array_equal(f, np.array(c["expected"]), err_msg=c["name"])
+        if "expected_keep_unresolved" in c:
+            fk = oracle.amf(g, c["smax"], keep_unresolved=True)
+            np.testing.assert_array_equal(fk, np.array(c["expected_keep_unresolved"]))
+        if "pixel" in c:
+            y, x = c["pixel"]
+            assert f[y, x] == c["expected_pixel"], c["name"]
+            assert oracle.amf_pixel(g, c["smax"], y, x) == c["expected_pixel"]
+
+
+@pytest.mark.parametrize("smax", [3, 5])
+def test_amf_exhaustive_binary_3x3(smax):
+    for code in range(512):
+        bits = [(code >> i) & 1 for i in range(9)]
+        g = (np.array(bits, dtype=np.uint8).reshape(3, 3) * 200 + 20)
+        for keep in (False, True):
+            ref, _ = amf_brute(g, smax, keep)
+            np.testing.assert_array_equal(oracle.amf(g, smax, keep_unresolved=keep), ref)
+
+
+def test_amf_exhaustive_ternary_2x3():
+    for code in range(3 ** 6):
+        vals, c = [], code
+        for _ in range(6):
+            vals.append(c % 3)
+            c //= 3
+        g = np.array(vals, dtype=np.uint16).reshape(2, 3) * 1000 + 7
+        for smax in (3, 5, 7):
+            ref, _ = amf_brute(g, smax)
+            np.testing.assert_array_equal(oracle.amf(g, smax), ref)
+
+
+def test_amf_random_tiny_vs_brute():
+    rng = np.random.default_rng(7)
+    for trial in range(120):
+        H, W = int(rng.integers(1, 10)), int(rng.integers(1, 10))
+        levels = int(rng.integers(2, 6))
+        smax = int(rng.choice([3, 5, 7, 9, 11]))
+        g = rng.integers(0, levels, size=(H, W)).astype(np.uint8) * (250 // (levels - 1))
+        if trial % 3 == 0:  # continuous values with impulses
+            g = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+            g[rng.random((H, W)) < 0.3] = 255
+        keep = bool(trial % 2)
+        ref, kref = amf_brute(g, smax, keep)
+        f, kk = oracle.amf(g, smax, keep_unresolved=keep, return_k=True)
+        np.testing.assert_array_equal(f, ref)
+        np.testing.assert_array_equal(kk, kref)
+
+
+def _amf_by_scipy(g, smax, keep=False):
+    """Algorithm 1 step 6 in its whole-image mask form, order statistics from scipy."""
+    import scipy.ndimage as ndi
+    g = g.astype(np.int64)
+    f = g.copy()
+    t = np.zeros(g.shape, dtype=bool)
+    zmed = None
+    for k in range(3, smax + 1, 2):
+        zmin = ndi.minimum_filter(g, size=k, mode="reflect")
+        zmax = ndi.maximum_filter(g, size=k, mode="reflect")
+        zmed = ndi.median_filter(g, size=k, mode="reflect")
+        lvl_a = (zmed > zmin) & (zmax > zmed) & ~t
+        z_b = (g > zmin) & (zmax > g)
+        f[lvl_a & z_b] = g[lvl_a & z_b]
+        f[lvl_a & ~z_b] = zmed[lvl_a & ~z_b]
+        t |= lvl_a
+    if not keep:
+        f[~t] = zmed[~t]
+    return f
+
+
+@pytest.mark.parametrize("smax,dtype,density", [(3, np.uint8, 0.3), (5, np.uint8, 0.5),
+                                                 (7, np.uint16, 0.6), (11, np.uint16, 0.7)])
+def test_amf_matches_library_order_statistics(smax, dtype, density):
+    rng = np.random.default_rng(smax)
+    maxv = 255 if dtype == np.uint8 else 4095
+    g = rng.integers(0, maxv + 1, size=(37, 53)).astype(dtype)
+    u = rng.random(g.shape)
+    g[u < density / 2] = 0
+    g[(u >= density / 2) & (u < density)] = maxv
+    # a flat patch forces growth all the way to Smax
+    g[5:20, 10:30] = maxv // 3
+    for keep in (False, True):
+        np.testing.assert_array_equal(oracle.amf(g, smax, keep_unresolved=keep),
+                                      _amf_by_scipy(g, smax, keep))
+
+
+def test_amf_invariants():
+    rng = np.random.default_rng(11)
+    # constant image passes through unchanged
+    for v in (0, 17, 255):
+        g = np.full((9, 14), v, np.uint8)
+        np.testing.assert_array_equal(oracle.amf(g, 7), g)
+    # isolated impulses on a flat background are replaced by the window median
+    g = np.full((21, 21), 90, np.uint8)
+    g[5, 5], g[15, 9], g[10, 17] = 255, 0, 255
+    np.testing.assert_array_equal(oracle.amf(g, 5), np.full_like(g, 90))
+    # isolated impulse on a varied background: output equals its 3x3 median
+    g = rng.integers(60, 200, size=(15, 15)).astype(np.uint8)
+    g[7, 7] = 255
+    win = np.sort(g[6:9, 6:9].ravel())
+    assert win[4] > win[0]
+    assert oracle.amf(g, 3)[7, 7] == win[4]
+    # output within [min g, max g]; a pixel strictly inside its 3x3 range with level A
+    # holding is unchanged
+    g = rng.integers(0, 4096, size=(40, 31)).astype(np.uint16)
+    g[rng.random(g.shape) < 0.4] = 4095
+    f, kk = oracle.amf(g, 9, return_k=True)
+    assert f.min() >= g.min() and f.max() <= g.max()
+    import scipy.ndimage as ndi
+    lo = ndi.minimum_filter(g, 3, mode="reflect")
+    hi = ndi.maximum_filter(g, 3, mode="reflect")
+    keep = (kk == 3) & (g > lo) & (g < hi)
+    np.testing.assert_array_equal(f[keep], g[keep])
+
+
+def test_amf_pixel_matches_full():
+    rng = np.random.default_rng(3)
+    g = rng.integers(0, 4096, size=(33, 29)).astype(np.uint16)
+    g[rng.random(g.shape) < 0.45] = 0
+    f = oracle.amf(g, 11)
+    for _ in range(60):
+        y, x = int(rng.integers(0, 33)), int(rng.integers(0, 29))
+        assert oracle.amf_pixel(g, 11, y, x) == f[y, x]
+
+
+# ------------------------------------------------------------------------ Wiener
+def _round_half_up_fraction(q: Fraction) -> int:
+    return int((q + Fraction(1, 2)).__floor__())
+
+
+@pytest.mark.parametrize("w", [1, 3, 5])
+def test_wiener_exact_rational(w):
+    rng = np.random.default_rng(w)
+    for H, W in [(1, 1), (1, 7), (6, 1), (5, 8), (9, 6)]:
+        f = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+        res = oracle.wiener(f, w)
+        y_ex, nu2_ex, var = wiener_exact(f, w)
+        # sum of D is n^2 * sum of local variances, exactly
+        n = w * w
+        assert res.sumD == sum(var[y][x] for y in range(H) for x in range(W)) * n * n
+        assert res.nu2 == pytest.approx(float(nu2_ex), rel=4e-16, abs=0)
+        # with the binary64 noise variance fed back in exactly, y matches per pixel
+        y_ex2, _, _ = wiener_exact(f, w, noise_var=Fraction(res.nu2))
+        for y in range(H):
+            for x in range(W):
+                assert abs(res.y64[y, x] - float(y_ex2[y, x])) <= 1e-9 * max(1.0, abs(float(y_ex2[y, x])))
+
+
+def test_wiener_noise_variance_is_correctly_converted():
+    # nu2 = fl(fl(sumD) / (n^2 H W)); Python's int->float is correctly rounded
+    rng = np.random.default_rng(5)
+    f = rng.integers(0, 65536, size=(128, 160)).astype(np.uint16)
+    res = oracle.wiener(f, 7)
+    assert res.sumD > 2 ** 53                  # exercises the rounding of the conversion
+    assert res.nu2 == float(res.sumD) / float(49 * 49 * 128 * 160)
+
+
+def test_wiener_constant_and_limits():
+    for w in (3, 5, 7):
+        f = np.full((12, 9), 77, np.uint8)
+        r = oracle.wiener(f, w)
+        assert r.nu2 == 0.0
+        np.testing.assert_array_equal(r.out64, f)
+        np.testing.assert_array_equal(r.out32, f)
+        r = oracle.wiener(f, w, noise_var=5.0)
+        np.testing.assert_array_equal(r.out64, f)
+    rng = np.random.default_rng(2)
+    f = rng.integers(0, 4096, size=(23, 19)).astype(np.uint16)
+    # noise variance 0 -> identity
+    r = oracle.wiener(f, 5, noise_var=0.0, bits=12)
+    np.testing.assert_array_equal(r.out64, f)
+    np.testing.assert_array_equal(r.out32, f)
+    assert np.max(np.abs(r.y64 - f)) < 1e-9
+    # huge noise variance -> box mean, rounded half up (exact integer rounding)
+    S1, _ = oracle.wiener_stats(f, 5)
+    r = oracle.wiener(f, 5, noise_var=1e30, bits=12)
+    expect = (2 * S1.astype(np.int64) + 25) // 50
+    np.testing.assert_array_equal(r.out64.astype(np.int64), expect)
+
+
+@pytest.mark.parametrize("w", [3, 5, 7])
+def test_wiener_checkerboard_closed_form(w):
+    # c +- d checkerboard: interior windows hold one more cell of the centre's
+    # colour, so mu = c +- d/n and sigma2 = d^2 (1 - 1/n^2): D = (n^2 - 1) d^2.
+    c, d = 1000, 37
+    H = W = 3 * w + 4
+    yy, xx = np.mgrid[0:H, 0:W]
+    f = np.where((yy + xx) % 2 == 0, c + d, c - d).astype(np.uint16)
+    S1, D = oracle.wiener_stats(f, w)
+    n = w * w
+    r = w // 2
+    inner = (slice(r, H - r), slice(r, W - r))
+    np.testing.assert_array_equal(D[inner], np.full_like(D[inner], (n * n - 1) * d * d))
+    centre_sign = np.where((yy + xx) % 2 == 0, 1, -1)[inner]
+    np.testing.assert_array_equal(S1[inner].astype(np.int64), n * c + centre_sign * d)
+
+
+@pytest.mark.parametrize("w", [3, 5])
+def test_wiener_ramp_closed_form(w):
+    # f = a*x + b: every interior window has variance a^2 r(r+1)/3
+    a, b = 7, 11
+    H, W = 9, 20
+    f = (a * np.arange(W)[None, :] + b + np.zeros((H, 1), np.int64)).astype(np.uint16)
+    S1, D = oracle.wiener_stats(f, w)
+    n, r = w * w, w // 2
+    inner = (slice(r, H - r), slice(r, W - r))
+    assert np.all(D[inner] == n * n * a * a * r * (r + 1) // 3)
+    assert np.all(S1[inner] == n * f[inner])
+
+
+def test_wiener_matches_scipy_with_zero_border():
+    from scipy.signal import wiener as scipy_wiener
+    rng = np.random.default_rng(9)
+    for w in (3, 5, 7):
+        f = rng.integers(0, 256, size=(31, 44)).astype(np.uint8)
+        r = oracle.wiener(f, w, border_zero=True)
+        ref = scipy_wiener(f.astype(np.float64), mysize=w)
+        np.testing.assert_allclose(r.y64, ref, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("bits,w", [(8, 3), (8, 7), (12, 5), (12, 7), (16, 3), (16, 7)])
+def test_wiener_binary32_twin_error_bound(bits, w):
+    rng = np.random.default_rng(bits * 10 + w)
+    maxv = (1 << bits) - 1
+    dtype = np.uint8 if bits == 8 else np.uint16
+    base = rng.integers(0, maxv + 1, size=(60, 70))
+    smooth = (base + np.roll(base, 1, 0) + np.roll(base, 1, 1)) // 3
+    f = np.where(rng.random((60, 70)) < 0.5, base, smooth).astype(dtype)
+    r = oracle.wiener(f, w, bits=bits)
+    bound = maxv * 2.0 ** -20
+    assert np.max(np.abs(r.y32.astype(np.float64) - r.y64)) <= bound
+    # integer outputs agree except where binary64 sits within the bound of a tie
+    diff = r.out32.astype(np.int64) != r.out64.astype(np.int64)
+    frac = r.y64 - np.floor(r.y64)
+    assert np.all(np.abs(frac[diff] - 0.5) <= bound)
+    assert np.all(np.abs(r.out64.astype(np.float64) - r.y64) <= 0.5 + 1e-12)
+
+
+def test_wiener_output_within_local_range():
+    rng = np.random.default_rng(4)
+    f = rng.integers(0, 4096, size=(25, 30)).astype(np.uint16)
+    import scipy.ndimage as ndi
+    for w in (3, 5):
+        r = oracle.wiener(f, w, bits=12)
+        lo = ndi.minimum_filter(f, w, mode="reflect")
+        hi = ndi.maximum_filter(f, w, mode="reflect")
+        assert np.all(r.out64 >= lo) and np.all(r.out64 <= hi)
+        # y lies between mu and f
+        S1, _ = oracle.wiener_stats(f, w)
+        mu = S1 / (w * w)
+        assert np.all((r.y64 - mu) * (f - mu) >= -1e-9)
+        assert np.all(np.abs(r.y64 - mu) <= np.abs(f - mu) + 1e-9)
+
+
+def test_hybrid_is_wiener_of_amf():
+    rng = np.random.default_rng(8)
+    g = rng.integers(0, 256, size=(20, 24)).astype(np.uint8)
+    g[rng.random(g.shape) < 0.2] = 255
+    f, r = oracle.hybrid(g, 7, 3)
+    np.testing.assert_array_equal(f, oracle.amf(g, 7))
+    r2 = oracle.wiener(f, 3)
+    np.testing.assert_array_equal(r.out64, r2.out64)
