@@ -1,0 +1,452 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid denoiser (adaptive median -> Wiener) on GB300.
+
+One step = one pass of the whole hot path (adaptive median with window
+growth, Wiener statistics, noise-variance reduction, Wiener apply) over one
+input of the chosen workload, through the C ABI.  Prints ONE JSON line.
+
+Workloads (seeded synthetic phantoms, see synth/):
+  paper1620  (default) 1620x1620 uint8, Gaussian sigma 20 + salt&pepper 0.20,
+             Smax 9, 5x5 Wiener, noise variance estimated.  The image is the
+             size of the paper's 2.5 MB medical image (Section V).
+  plain512   512x512 uint8, sigma 10, density 0.05, Smax 7, 3x3 Wiener.
+  stress4096 4096x4096 12-bit, sigma 40, density 0.40, Smax 11, 5x5 Wiener.
+  batched    256 uneven 12-bit slices (256^2..1024^2), per-slice parameters,
+             one persistent launch replayed as a CUDA graph.
+
+Timing: W untimed warm-up steps, then K steps between barrier +
+synchronize, timed with CUDA events on the launching stream.  Inputs rotate
+over enough device copies that every step reads data not resident in the
+129 MB L2.  `e2e` runs the same workload through hybrid_denoise_host (pinned
+host buffers, copies inside the timed region).  `--impl reference` times the
+CPU oracle instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "hybrid AMF+Wiener Mpixel/s on 1 GB300 (batched vs plain); p50/p99 served latency"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+# --------------------------------------------------------------------------- helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_05371_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch from an ncu capture, if taken on the current kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as fh:
+        rec = json.load(fh)
+    ent = rec.get(workload)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workloads
+def build_workload(name: str, rank: int):
+    """Host images + parameters.  Rank r draws its own replica (distinct seeds)."""
+    import synth
+    if name in synth.CONFIGS:
+        spec = synth.CONFIGS[name]
+        if rank:
+            spec = synth.SliceSpec(**{**spec.__dict__, "phantom_seed": spec.phantom_seed + 1000 * rank,
+                                      "noise_seed": spec.noise_seed + 1000 * rank})
+        clean = spec.clean()
+        return [(spec, spec.noisy(clean))]
+    if name == "batched":
+        specs = synth.batch_specs(256, master_seed=400 + rank)
+        return [(s, s.noisy()) for s in specs]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(name: str, items) -> dict:
+    px = sum(s.H * s.W for s, _ in items)
+    if name == "batched":
+        return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
+                            "density U[0.01,0.5], Smax {5,7,9,11}, Wiener {3,5,7}, one persistent launch "
+                            "(CUDA graph)", "images": len(items), "megapixels": round(px / 1e6, 3)}
+    s = items[0][0]
+    return {"workload": f"{name}: {s.H}x{s.W} {s.dtype} {s.bits}-bit, sigma {s.sigma:g}, s&p {s.density:g}, "
+                        f"Smax {s.smax}, Wiener {s.wiener_w}x{s.wiener_w}, noise variance estimated",
+            "H": s.H, "W": s.W, "smax": s.smax, "wiener_w": s.wiener_w, "megapixels": round(px / 1e6, 3)}
+
+
+def algorithmic_bytes(items) -> int:
+    """Read the noisy input once and write the result once."""
+    return sum(2 * s.H * s.W * (1 if s.dtype == "u8" else 2) for s, _ in items)
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample_rate(items, budget_s: float):
+    """Oracle Mpx/s on a bounded sample: whole images (or row bands) until ~budget_s."""
+    import oracle
+    done_px, t_total = 0, 0.0
+    descr = []
+    for spec, g in items:
+        # calibrate on a 32-row band, then size the band to the remaining budget
+        rows = min(spec.H, 32)
+        t0 = time.perf_counter()
+        oracle.hybrid(g[:rows], spec.smax, spec.wiener_w, bits=spec.bits)
+        dt = time.perf_counter() - t0
+        done_px += rows * spec.W
+        t_total += dt
+        remaining = budget_s - t_total
+        if remaining <= 0:
+            descr.append(f"{rows} rows of {spec.H}x{spec.W}")
+            break
+        per_row = dt / rows
+        more = int(min(spec.H, max(1, remaining / per_row)))
+        if more > rows:
+            t0 = time.perf_counter()
+            oracle.hybrid(g[:more], spec.smax, spec.wiener_w, bits=spec.bits)
+            t_total += time.perf_counter() - t0
+            done_px += more * spec.W
+            rows = more
+        descr.append(f"{rows} rows of {spec.H}x{spec.W}")
+        if t_total >= budget_s:
+            break
+    return done_px / t_total / 1e6, t_total, "; ".join(descr[:4]) + (" ..." if len(descr) > 4 else "")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    items = build_workload(args.workload, 0)
+    per_step = max(0.2, min(5.0, args.ref_budget / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(items, per_step)
+    rates, tsum, descr = [], 0.0, ""
+    for _ in range(args.steps):
+        r, t, descr = oracle_sample_rate(items, per_step)
+        rates.append(r)
+        tsum += t
+    value = statistics.median(rates)
+    px_step = describe(args.workload, items)["megapixels"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * px_step / value, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8" if items[0][0].dtype == "u8" else "u16", "data": "synthetic",
+        "config": describe(args.workload, items),
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step ~{per_step:.1f} s of the C oracle (single thread) on {descr}"},
+        "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="paper1620",
+                    choices=["paper1620", "plain512", "stress4096", "batched"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=90.0, help="total seconds of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    sys.path.insert(0, ROOT)
+    import __graft_entry__
+    __graft_entry__._buildlib().build()
+    import paper_2005_05371_gb300 as hd
+
+    items = build_workload(args.workload, rank)
+    cfg = describe(args.workload, items)
+    stream = torch.cuda.current_stream(dev)
+
+    def to_dev(a):
+        t = torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a)
+        return t.to(dev)
+
+    def params_of(spec):
+        return hd.Params(spec.smax, spec.wiener_w, -1.0, hd.HD_BORDER_SYMMETRIC, hd.HD_UNRESOLVED_ZMED, spec.bits)
+
+    step_bytes = algorithmic_bytes(items)
+    copies = max(1, math.ceil(3 * L2_BYTES / step_bytes)) if args.workload != "batched" else 2
+    px_per_step = sum(s.H * s.W for s, _ in items)
+
+    if args.workload == "batched":
+        # `copies` independent batch plans over distinct device buffers
+        plans, bufs = [], []
+        for c in range(copies):
+            its = []
+            for spec, g in items:
+                src = to_dev(g)
+                dst = torch.empty_like(src)
+                its.append((src, dst, params_of(spec)))
+            bufs.append(its)
+            plans.append(hd.BatchPlan(its))
+
+        def step(i):
+            plans[i % copies].launch(stream)
+
+        launches_per_step = 1
+        # plain: per-slice launch loop (one hybrid_denoise call per slice) on the same data
+        spec0 = None
+        ws_plain = [hd._workspace(hd.hybrid_workspace_size(s.H, s.W, hd.HD_U16, params_of(s)), dev)
+                    for s, _ in items]
+
+        def plain_step(i):
+            its = bufs[i % copies]
+            for (src, dst, p), ws in zip(its, ws_plain):
+                hd.hybrid_denoise(src, dst, p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                                  workspace=ws, stream=stream)
+    else:
+        spec, g = items[0]
+        p = params_of(spec)
+        srcs = [to_dev(g) for _ in range(copies)]
+        dsts = [torch.empty_like(srcs[0]) for _ in range(copies)]
+        code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
+        ws = hd._workspace(hd.hybrid_workspace_size(spec.H, spec.W, code, p), dev)
+
+        def step(i):
+            j = i % copies
+            hd.hybrid_denoise(srcs[j], dsts[j], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                              workspace=ws, stream=stream)
+
+        launches_per_step = 1
+        plain_step = None
+
+    def timed(fn, K, W):
+        for i in range(W):
+            fn(i)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        t0 = time.perf_counter()
+        for i in range(K):
+            evs[i][0].record(stream)
+            fn(W + i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        per = [a.elapsed_time(b) for a, b in evs]
+        return sum(per), per, wall
+
+    with ClockSampler(local) as clk:
+        total_ms, per_ms, wall = timed(step, args.steps, args.warmup)
+    clocks = clk.summary()
+    status = hd.hd_get_device_error(stream)
+    if status != hd.HD_OK:
+        raise SystemExit(f"device error after the timed region: {hd.hd_status_str(status)}")
+
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    ms_per_step = total_ms / args.steps
+    value = world * px_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # dominant (and only) kernel: one persistent launch per step
+    peak, peak_kind = peaks()
+    achieved = step_bytes / (ms_per_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+                "kernel": "hd_persistent_kernel", "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": step_bytes}
+
+    extra = {}
+    if plain_step is not None:
+        plain_ms, _, _ = timed(plain_step, max(3, args.steps // 5), args.warmup)
+        extra["plain_loop"] = {"value": round(px_per_step * max(3, args.steps // 5) / (plain_ms / 1e3) / 1e6, 1),
+                               "unit": "Mpixel/s", "launches_per_step": len(items)}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e and args.workload != "batched":
+        spec, g = items[0]
+        p = params_of(spec)
+        code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
+        tdt = torch.uint8 if spec.dtype == "u8" else torch.int16
+        hsrc = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory()
+        hdst = torch.empty(hsrc.shape, dtype=tdt).pin_memory()
+        wsh = hd._workspace(hd.hybrid_host_workspace_size(spec.H, spec.W, code, p), dev)
+
+        def host_step(i):
+            hd.hybrid_denoise_host(hsrc, hdst, p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                                   workspace=wsh, stream=stream)
+        for i in range(args.warmup):
+            host_step(i)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            host_step(i)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        nbytes = g.nbytes
+        e2e = {"value": round(world * px_per_step * args.steps / dt / 1e6, 2), "unit": "Mpixel/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "api": "hybrid_denoise_host (pinned host buffers)"}
+    elif not args.no_e2e:
+        # batched end to end: pinned host slices -> device, one graph launch, device -> host
+        hs = [torch.from_numpy(g.view(np.int16)).pin_memory() for _, g in items]
+        ho = [torch.empty_like(h).pin_memory() for h in hs]
+        its = bufs[0]
+
+        def e2e_step(i):
+            for h, (src, _, _) in zip(hs, its):
+                src.copy_(h, non_blocking=True)
+            plans[0].launch(stream)
+            for h, (_, dst, _) in zip(ho, its):
+                h.copy_(dst, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+        for i in range(args.warmup):
+            e2e_step(i)
+        t0 = time.perf_counter()
+        K2 = max(3, args.steps // 5)
+        for i in range(K2):
+            e2e_step(i)
+        dt = time.perf_counter() - t0
+        nb = sum(g.nbytes for _, g in items)
+        e2e = {"value": round(world * px_per_step * K2 / dt / 1e6, 2), "unit": "Mpixel/s",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+               "api": "copy_ + hd_batch_plan_launch (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget)
+        cpu = {"value": round(rate, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+               "sample": f"C oracle, single thread, {secs:.1f} s on {descr}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8" if items[0][0].dtype == "u8" else "u16", "data": "synthetic",
+            "config": {**cfg, "parallelism": f"replicas x{world}",
+                       "l2": f"inputs rotate over {copies} device copies ({copies * step_bytes / 2**20:.0f} MiB "
+                             f"of algorithmic traffic > 129 MB L2)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks, **extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * hybrid_denoise.h -- C ABI of the GB300 hybrid multi-noise denoiser.
+ *
+ * Method: Youssef, Mahmoud, El-Horbaty, "A Parallel Hybrid Technique for
+ * Multi-Noise Removal from Grayscale Medical Images".  The hybrid is an
+ * adaptive median filter (Algorithm 1, step 6; Section IV) followed by a
+ * Wiener filter (Algorithm 1, step 4d), here in its spatial local-statistics
+ * form with the noise variance estimated as the mean local variance.
+ *
+ * Conventions for every entry point
+ *   - Images are H x W, row-major, with a row pitch in BYTES (>= W * element
+ *     size).  HD_U8 images hold 8-bit values; HD_U16 images hold values of
+ *     `bits` bits (1..16; values above 2^bits - 1 are outside the contract).
+ *   - src, dst, workspace and every optional output are DEVICE pointers owned
+ *     by the caller (hybrid_denoise_host is the one exception: src and dst are
+ *     host pointers there).  The library allocates no device memory.
+ *   - src and dst must not overlap: the adaptive median reads only the noisy
+ *     input (the listing's neighbourhood statistics are taken of g, never of
+ *     the partly filtered copy).
+ *   - Work is enqueued on `stream` (NULL = legacy default stream).  Argument
+ *     errors are returned synchronously before anything is enqueued.  Launch
+ *     failures return HD_ERR_CUDA.  Faults seen by the kernels while running
+ *     (a bounded wait that ran out) are latched in a per-device error word and
+ *     reported by hd_get_device_error.
+ *   - A workspace must be zero-filled before its first use (cudaMemset); every
+ *     call leaves the queue counters in it zeroed again for the next call.
+ *     A call that did not run to completion (launch error, abort) leaves it in
+ *     an unknown state: zero it again.
+ *   - Calls that share a workspace must not overlap in time on the device.
+ *   - No C++ exception crosses this boundary.
+ */
+#ifndef HYBRID_DENOISE_H
+#define HYBRID_DENOISE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *hd_stream_t;
+
+typedef enum {
+    HD_OK = 0,
+    HD_ERR_ARG = 1,        /* null pointer, bad size, bad pitch, overlap, bad enum */
+    HD_ERR_SMAX = 2,       /* Smax not an odd integer in [3, HD_SMAX_MAX] (Alg. 1, step 6a) */
+    HD_ERR_WINDOW = 3,     /* Wiener window not odd in [1, HD_WIENER_W_MAX] */
+    HD_ERR_DTYPE = 4,      /* unknown dtype or bits outside 1..16 (8 for HD_U8) */
+    HD_ERR_WORKSPACE = 5,  /* workspace missing, misaligned or smaller than required */
+    HD_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+    HD_ERR_TIMEOUT = 7,    /* a bounded device-side wait ran out (hd_get_device_error) */
+    HD_ERR_OVERFLOW = 8    /* size beyond the library's limits */
+} hd_status;
+
+typedef enum { HD_U8 = 0, HD_U16 = 1 } hd_dtype;
+
+/* Border rule for out-of-image window samples.  SYMMETRIC: half-sample
+ * reflection with period 2N (... 1 0 | 0 1 ... N-1 | N-1 N-2 ...), used by both
+ * stages.  ZERO: samples outside the image read 0 but still count in the
+ * window size n = w*w; Wiener stage only. */
+typedef enum { HD_BORDER_SYMMETRIC = 0, HD_BORDER_ZERO = 1 } hd_border;
+
+/* Pixels that fail level A for every window up to Smax.  ZMED: they take the
+ * median of the Smax window (textbook adaptive median; replaces isolated
+ * impulses on flat backgrounds).  KEEP: they keep their input value (literal
+ * reading of Algorithm 1, where the working copy starts as the input). */
+typedef enum { HD_UNRESOLVED_ZMED = 0, HD_UNRESOLVED_KEEP = 1 } hd_unresolved;
+
+#define HD_SMAX_MAX 15
+#define HD_WIENER_W_MAX 15
+#define HD_DIM_MAX 65535          /* largest H or W */
+
+/* Filter parameters (Algorithm 1: Smax = 11 in the paper's runs). */
+typedef struct {
+    int smax;            /* adaptive median: largest window, odd, 3..HD_SMAX_MAX */
+    int wiener_w;        /* Wiener window side, odd, 1..HD_WIENER_W_MAX */
+    double noise_var;    /* Wiener noise variance nu2 (in squared LSB); < 0: estimate it
+                            as the mean over all pixels of the local variance */
+    int border;          /* hd_border, Wiener stage (the median always reflects) */
+    int unresolved;      /* hd_unresolved */
+    int bits;            /* significant bits: 8 for HD_U8; 1..16 for HD_U16 */
+} hd_params;
+
+/* One image and where its result goes. */
+typedef struct {
+    const void *src;         /* device, H rows of src_pitch bytes */
+    void *dst;               /* device, H rows of dst_pitch bytes, same dtype */
+    int H, W;                /* 1..HD_DIM_MAX each */
+    size_t src_pitch;        /* bytes, >= W * element size */
+    size_t dst_pitch;        /* bytes, >= W * element size */
+    int dtype;               /* hd_dtype */
+    hd_params p;
+    double *noise_var_out;   /* optional device pointer: receives the nu2 that was used */
+    float *y_out;            /* optional device pointer: H x W float plane (pitch W*4) of
+                                the unrounded Wiener output */
+} hd_image;
+
+/* ---------------------------------------------------------------- stages
+ * Adaptive median filter (Algorithm 1, step 6): for k = 3, 5, ..., Smax over
+ * the k x k window of src, level A (zmin < zmed < zmax, strict) decides
+ * whether the pixel is processed at k; level B (zmin < zxy < zmax, strict)
+ * keeps zxy, else outputs zmed.  The first k that passes level A wins.
+ * Output is exact (integer order statistics).  Needs no workspace.
+ * Uses img->p.smax and img->p.unresolved; the Wiener fields are ignored. */
+hd_status amf_filter(const hd_image *img, hd_stream_t stream);
+
+/* Wiener filter of an already median-filtered image (Algorithm 1, step 4d;
+ * local-statistics form).  Over the w x w window, n = w*w, with exact integer
+ * S1 = sum f, S2 = sum f^2 and D = n*S2 - S1^2:
+ *   mu = S1/n, sigma2 = D/n^2,
+ *   nu2 = noise_var if >= 0, else fl(fl(sum of D over all pixels) / (n^2 H W)),
+ *   y = mu + max(sigma2 - nu2, 0) / max(sigma2, nu2) * (f - mu)  (y = mu if both 0),
+ *   dst = min(2^bits - 1, floor(y + 0.5)).
+ * The sums are exact integers, nu2 is binary64, the gain and y are binary32
+ * with a fixed evaluation order (documented with the kernel).
+ * workspace: device, >= wiener_workspace_size() bytes, 256-byte aligned. */
+hd_status wiener_filter(const hd_image *img, void *workspace, size_t ws_bytes,
+                        hd_stream_t stream);
+hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
+
+/* The hybrid (Algorithm 1, step 4, without the contrast stretch of step 4e):
+ * dst = Wiener(AdaptiveMedian(src)).  One persistent kernel launch: the
+ * median output stays in the workspace (L2-resident for images up to tens of
+ * MB); with a caller-supplied noise_var >= 0 the whole hybrid is one pass and
+ * needs no workspace.  Exactly one kernel is enqueued per call.
+ * workspace: device, >= hybrid_workspace_size() bytes, 256-byte aligned. */
+hd_status hybrid_denoise(const hd_image *img, void *workspace, size_t ws_bytes,
+                         hd_stream_t stream);
+hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
+
+/* The hybrid over host buffers: img->src and img->dst are HOST pointers
+ * (pinned memory gives overlap-free full-speed copies; pageable works).  The
+ * call copies src into the workspace, runs hybrid_denoise there, copies the
+ * result back to dst and waits for the stream.  Returns after dst is written.
+ * workspace: device, >= hybrid_host_workspace_size() bytes. */
+hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_bytes,
+                              hd_stream_t stream);
+hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p,
+                                     size_t *bytes);
+
+/* ---------------------------------------------------------------- batches
+ * Many images of uneven sizes and per-image parameters in ONE persistent
+ * kernel launch: a device work queue of (image, phase, tile) items where an
+ * image's Wiener tiles start as soon as that image's median tiles are done,
+ * so one image's Wiener overlaps another's median.  Each result is
+ * bit-identical to the same image through hybrid_denoise (integer
+ * reductions make the order irrelevant).
+ * hybrid_denoise_batched copies the n descriptors into the workspace on
+ * `stream` (not capturable in a CUDA graph; use a plan for that). */
+hd_status hybrid_denoise_batched(const hd_image *imgs, int n, void *workspace,
+                                 size_t ws_bytes, hd_stream_t stream);
+hd_status hybrid_batched_workspace_size(const hd_image *imgs, int n, size_t *bytes);
+
+/* A batch plan fixes the descriptors once (synchronous copy into the
+ * workspace at creation) and replays the batch as a CUDA graph (memset of the
+ * queue counters + the persistent kernel).  The plan holds host memory only;
+ * the workspace stays owned by the caller and must outlive the plan. */
+typedef struct hd_batch_plan hd_batch_plan;
+hd_status hd_batch_plan_create(const hd_image *imgs, int n, void *workspace, size_t ws_bytes,
+                               hd_batch_plan **plan);
+hd_status hd_batch_plan_launch(hd_batch_plan *plan, hd_stream_t stream);
+hd_status hd_batch_plan_destroy(hd_batch_plan *plan);
+
+/* ---------------------------------------------------------------- tuning
+ * Tile shape of the persistent kernel (output pixels per work item) and the
+ * grid size in CTAs per SM.  tile_w: multiple of 8 in [8, 256]; tile_h in
+ * [4, 128]; ctas_per_sm in [1, 8] (0 = as many as fit).  Applies to later
+ * launches in this process. */
+typedef struct {
+    int tile_w;
+    int tile_h;
+    int ctas_per_sm;
+} hd_tuning;
+hd_status hd_set_tuning(const hd_tuning *t);
+hd_status hd_get_tuning(hd_tuning *t);
+
+/* Number of polls (>= 256 ns apart after the first 64) before a device-side
+ * wait of a Wiener tile on its image's median tiles gives up, latches
+ * HD_ERR_TIMEOUT and skips the tile.  0 restores the default (about 2 s).
+ * A tiny limit makes waits run out on purpose, which is how the error path
+ * is tested without stalling a GPU. */
+hd_status hd_set_spin_limit(unsigned long long polls);
+
+/* ---------------------------------------------------------------- errors
+ * Synchronises `stream`, then returns and clears the device error word of the
+ * current device: HD_ERR_TIMEOUT if a bounded wait inside a kernel ran out,
+ * HD_ERR_CUDA if the stream reports an error, else HD_OK. */
+hd_status hd_get_device_error(hd_stream_t stream);
+const char *hd_status_str(hd_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYBRID_DENOISE_H */

@@ -1,0 +1,353 @@
+"""Python binding of the GB300 hybrid multi-noise denoiser (C ABI in libhd.so).
+
+The functions carry the C names (``amf_filter``, ``wiener_filter``,
+``hybrid_denoise``, ``hybrid_denoise_batched`` ...) and only marshal
+arguments: every stage runs in the CUDA kernels of ``libhd.so``.  Tensors are
+``torch`` CUDA tensors (uint8, or uint16 for 9..16-bit images); PyTorch is used
+for device memory and streams only.  If the library is missing or cannot be
+loaded the import fails loudly; there is no CPU fallback.
+
+Algorithm (Youssef, Mahmoud, El-Horbaty): adaptive median (Algorithm 1,
+step 6) followed by a local-statistics Wiener filter (Algorithm 1, step 4d).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhd.so")
+
+HD_OK, HD_ERR_ARG, HD_ERR_SMAX, HD_ERR_WINDOW, HD_ERR_DTYPE = 0, 1, 2, 3, 4
+HD_ERR_WORKSPACE, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_OVERFLOW = 5, 6, 7, 8
+HD_U8, HD_U16 = 0, 1
+HD_BORDER_SYMMETRIC, HD_BORDER_ZERO = 0, 1
+HD_UNRESOLVED_ZMED, HD_UNRESOLVED_KEEP = 0, 1
+HD_SMAX_MAX = 15
+HD_WIENER_W_MAX = 15
+
+# every symbol include/hybrid_denoise.h declares
+EXPORTS = [
+    "amf_filter", "wiener_filter", "wiener_workspace_size", "hybrid_denoise", "hybrid_workspace_size",
+    "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_batched",
+    "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
+    "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
+    "hd_status_str", "hd_version",
+]
+
+
+class hd_params(ctypes.Structure):
+    _fields_ = [("smax", ctypes.c_int), ("wiener_w", ctypes.c_int), ("noise_var", ctypes.c_double),
+                ("border", ctypes.c_int), ("unresolved", ctypes.c_int), ("bits", ctypes.c_int)]
+
+
+class hd_image(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("src_pitch", ctypes.c_size_t), ("dst_pitch", ctypes.c_size_t), ("dtype", ctypes.c_int),
+                ("p", hd_params), ("noise_var_out", ctypes.c_void_p), ("y_out", ctypes.c_void_p)]
+
+
+class hd_tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class HDError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {hd_status_str(status)} (status {status})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2005_05371_gb300/buildlib.py "
+                          "(the denoiser has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    img_p = ctypes.POINTER(hd_image)
+    par_p = ctypes.POINTER(hd_params)
+    sig = {
+        "amf_filter": ([img_p, P], I),
+        "wiener_filter": ([img_p, P, S, P], I),
+        "wiener_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
+        "hybrid_denoise": ([img_p, P, S, P], I),
+        "hybrid_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
+        "hybrid_denoise_host": ([img_p, P, S, P], I),
+        "hybrid_host_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
+        "hybrid_denoise_batched": ([img_p, I, P, S, P], I),
+        "hybrid_batched_workspace_size": ([img_p, I, ctypes.POINTER(S)], I),
+        "hd_batch_plan_create": ([img_p, I, P, S, ctypes.POINTER(P)], I),
+        "hd_batch_plan_launch": ([P, P], I),
+        "hd_batch_plan_destroy": ([P], I),
+        "hd_set_tuning": ([ctypes.POINTER(hd_tuning)], I),
+        "hd_get_tuning": ([ctypes.POINTER(hd_tuning)], I),
+        "hd_set_spin_limit": ([ctypes.c_ulonglong], I),
+        "hd_get_device_error": ([P], I),
+        "hd_status_str": ([I], ctypes.c_char_p),
+        "hd_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def hd_status_str(status: int) -> str:
+    return _lib.hd_status_str(int(status)).decode()
+
+
+def hd_version() -> int:
+    return _lib.hd_version()
+
+
+def _check(status: int, what: str):
+    if status != HD_OK:
+        raise HDError(status, what)
+
+
+# ----------------------------------------------------------------- helpers
+@dataclass
+class Params:
+    """Filter parameters (mirrors hd_params)."""
+    smax: int = 11
+    wiener_w: int = 5
+    noise_var: float = -1.0
+    border: int = HD_BORDER_SYMMETRIC
+    unresolved: int = HD_UNRESOLVED_ZMED
+    bits: int | None = None
+
+    def to_c(self, dtype_code: int) -> hd_params:
+        bits = self.bits if self.bits is not None else (8 if dtype_code == HD_U8 else 16)
+        return hd_params(int(self.smax), int(self.wiener_w), float(self.noise_var), int(self.border),
+                         int(self.unresolved), int(bits))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.uint8:
+        return HD_U8
+    if t.dtype in (torch.uint16, torch.int16):
+        return HD_U16
+    raise TypeError(f"unsupported tensor dtype {t.dtype}: use uint8 or uint16")
+
+
+def _pitch(t) -> int:
+    if t.dim() != 2:
+        raise ValueError("images are 2-D (H, W)")
+    if t.stride(1) != 1:
+        raise ValueError("image rows must be contiguous")
+    return t.stride(0) * t.element_size()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_image(src, dst, params: Params, noise_var_out=None, y_out=None) -> hd_image:
+    """hd_image for two CUDA tensors of the same dtype and shape."""
+    if src.shape != dst.shape or src.dtype != dst.dtype:
+        raise ValueError("src and dst must have the same shape and dtype")
+    code = _dtype_code(src)
+    H, W = src.shape
+    return hd_image(src.data_ptr(), dst.data_ptr(), H, W, _pitch(src), _pitch(dst), code, params.to_c(code),
+                    noise_var_out.data_ptr() if noise_var_out is not None else None,
+                    y_out.data_ptr() if y_out is not None else None)
+
+
+def _workspace(nbytes: int, device):
+    if nbytes == 0:
+        return None
+    torch = _torch()
+    # over-allocate so the pointer can be rounded up to 256 bytes; the library
+    # wants a zero-filled workspace on first use and leaves it zeroed
+    buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device=device)
+    return buf
+
+
+def _ws_ptr(buf) -> int | None:
+    if buf is None:
+        return None
+    p = buf.data_ptr()
+    return (p + 255) // 256 * 256
+
+
+def _ws_len(buf) -> int:
+    if buf is None:
+        return 0
+    p = buf.data_ptr()
+    return buf.numel() - ((p + 255) // 256 * 256 - p)
+
+
+# ----------------------------------------------------------------- stages
+def amf_filter(src, dst, smax: int = 11, unresolved: int = HD_UNRESOLVED_ZMED, bits: int | None = None,
+               stream=None):
+    """Adaptive median filter (Algorithm 1, step 6) of ``src`` into ``dst``."""
+    img = make_image(src, dst, Params(smax=smax, unresolved=unresolved, bits=bits))
+    _check(_lib.amf_filter(ctypes.byref(img), _stream_ptr(stream)), "amf_filter")
+    return dst
+
+
+def hybrid_workspace_size(H: int, W: int, dtype_code: int, params: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)), ctypes.byref(n)),
+           "hybrid_workspace_size")
+    return n.value
+
+
+def wiener_workspace_size(H: int, W: int, dtype_code: int, params: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.wiener_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)), ctypes.byref(n)),
+           "wiener_workspace_size")
+    return n.value
+
+
+def hybrid_host_workspace_size(H: int, W: int, dtype_code: int, params: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_host_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)),
+                                           ctypes.byref(n)), "hybrid_host_workspace_size")
+    return n.value
+
+
+def wiener_filter(src, dst, wiener_w: int = 5, noise_var: float = -1.0, border: int = HD_BORDER_SYMMETRIC,
+                  bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None):
+    """Local-statistics Wiener filter (Algorithm 1, step 4d) of ``src`` into ``dst``."""
+    p = Params(wiener_w=wiener_w, noise_var=noise_var, border=border, bits=bits)
+    img = make_image(src, dst, p, noise_var_out, y_out)
+    if workspace is None:
+        workspace = _workspace(wiener_workspace_size(img.H, img.W, img.dtype, p), src.device)
+    _check(_lib.wiener_filter(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace), _stream_ptr(stream)),
+           "wiener_filter")
+    return dst
+
+
+def hybrid_denoise(src, dst, smax: int = 11, wiener_w: int = 5, noise_var: float = -1.0,
+                   border: int = HD_BORDER_SYMMETRIC, unresolved: int = HD_UNRESOLVED_ZMED,
+                   bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None):
+    """Hybrid denoise: Wiener(AdaptiveMedian(src)) into ``dst`` (Algorithm 1, step 4)."""
+    p = Params(smax, wiener_w, noise_var, border, unresolved, bits)
+    img = make_image(src, dst, p, noise_var_out, y_out)
+    if workspace is None:
+        workspace = _workspace(hybrid_workspace_size(img.H, img.W, img.dtype, p), src.device)
+    _check(_lib.hybrid_denoise(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace), _stream_ptr(stream)),
+           "hybrid_denoise")
+    return dst
+
+
+def hybrid_denoise_host(src: np.ndarray, dst: np.ndarray, smax: int = 11, wiener_w: int = 5,
+                        noise_var: float = -1.0, border: int = HD_BORDER_SYMMETRIC,
+                        unresolved: int = HD_UNRESOLVED_ZMED, bits: int | None = None, workspace=None,
+                        stream=None):
+    """Hybrid denoise of HOST arrays (numpy or pinned CPU tensors): copies in, runs, copies out, waits."""
+    def ptr_pitch(a):
+        if isinstance(a, np.ndarray):
+            if a.ndim != 2 or a.strides[1] != a.itemsize:
+                raise ValueError("host image rows must be contiguous")
+            return a.ctypes.data, a.strides[0], (HD_U8 if a.dtype == np.uint8 else HD_U16), a.shape
+        return a.data_ptr(), _pitch(a), _dtype_code(a), tuple(a.shape)
+    sp, spitch, code, shape = ptr_pitch(src)
+    dp, dpitch, code2, shape2 = ptr_pitch(dst)
+    if code != code2 or shape != shape2:
+        raise ValueError("src and dst must have the same shape and dtype")
+    p = Params(smax, wiener_w, noise_var, border, unresolved, bits)
+    H, W = shape
+    img = hd_image(sp, dp, H, W, spitch, dpitch, code, p.to_c(code), None, None)
+    if workspace is None:
+        workspace = _workspace(hybrid_host_workspace_size(H, W, code, p), "cuda")
+    _check(_lib.hybrid_denoise_host(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace),
+                                    _stream_ptr(stream)), "hybrid_denoise_host")
+    return dst
+
+
+# ----------------------------------------------------------------- batches
+def _image_array(items) -> ctypes.Array:
+    """items: sequence of (src, dst, Params) or ready hd_image structs."""
+    arr = (hd_image * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = it if isinstance(it, hd_image) else make_image(*it)
+    return arr
+
+
+def hybrid_batched_workspace_size(items) -> int:
+    arr = _image_array(items)
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_batched_workspace_size(arr, len(arr), ctypes.byref(n)), "hybrid_batched_workspace_size")
+    return n.value
+
+
+def hybrid_denoise_batched(items, workspace=None, stream=None):
+    """Hybrid denoise of many images (uneven sizes, own parameters) in one persistent launch."""
+    arr = _image_array(items)
+    if workspace is None:
+        n = ctypes.c_size_t()
+        _check(_lib.hybrid_batched_workspace_size(arr, len(arr), ctypes.byref(n)), "hybrid_batched_workspace_size")
+        workspace = _workspace(n.value, "cuda")
+    _check(_lib.hybrid_denoise_batched(arr, len(arr), _ws_ptr(workspace), _ws_len(workspace),
+                                       _stream_ptr(stream)), "hybrid_denoise_batched")
+    return workspace
+
+
+class BatchPlan:
+    """hd_batch_plan: a batch fixed once and replayed as a CUDA graph."""
+
+    def __init__(self, items, workspace=None):
+        self._arr = _image_array(items)
+        if workspace is None:
+            n = ctypes.c_size_t()
+            _check(_lib.hybrid_batched_workspace_size(self._arr, len(self._arr), ctypes.byref(n)),
+                   "hybrid_batched_workspace_size")
+            workspace = _workspace(n.value, "cuda")
+        self.workspace = workspace
+        self._plan = ctypes.c_void_p()
+        _check(_lib.hd_batch_plan_create(self._arr, len(self._arr), _ws_ptr(workspace), _ws_len(workspace),
+                                         ctypes.byref(self._plan)), "hd_batch_plan_create")
+
+    def launch(self, stream=None):
+        _check(_lib.hd_batch_plan_launch(self._plan, _stream_ptr(stream)), "hd_batch_plan_launch")
+
+    def close(self):
+        if self._plan:
+            _lib.hd_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- tuning / errors
+def hd_set_tuning(tile_w: int, tile_h: int, ctas_per_sm: int = 0):
+    t = hd_tuning(tile_w, tile_h, ctas_per_sm)
+    _check(_lib.hd_set_tuning(ctypes.byref(t)), "hd_set_tuning")
+
+
+def hd_get_tuning() -> tuple[int, int, int]:
+    t = hd_tuning()
+    _check(_lib.hd_get_tuning(ctypes.byref(t)), "hd_get_tuning")
+    return t.tile_w, t.tile_h, t.ctas_per_sm
+
+
+def hd_set_spin_limit(polls: int = 0):
+    """Polls before a device-side wait gives up (0 restores the default of about 2 s)."""
+    _check(_lib.hd_set_spin_limit(int(polls)), "hd_set_spin_limit")
+
+
+def hd_get_device_error(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device error status."""
+    return _lib.hd_get_device_error(_stream_ptr(stream))

@@ -1,0 +1,546 @@
+// hd_api.cu -- host side of the C ABI declared in include/hybrid_denoise.h.
+//
+// Validates arguments, lays out the caller's workspace, builds the work-item
+// segments and launches the persistent kernel (hd_kernel.cu).  No device
+// memory is allocated here: every buffer comes from the caller.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hd_internal.h"
+#include "hybrid_denoise.h"
+
+using namespace hd;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kTicketBytes = 256;
+constexpr unsigned long long kSpinLimit = 8000000ull;   // polls of >= 256 ns: about 2 s
+
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::mutex g_tune_mu;
+hd_tuning g_tune = {64, 32, 0};
+unsigned long long g_spin_limit = kSpinLimit;
+
+hd_tuning current_tuning()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+
+int elem_size(int dtype) { return dtype == HD_U8 ? 1 : 2; }
+
+// Checks shared by every entry point.  `need_amf` / `need_wiener` select the
+// parameter checks of the stages the call runs.
+hd_status check_image(const hd_image *img, bool need_amf, bool need_wiener, bool host_buffers)
+{
+    if (!img) return HD_ERR_ARG;
+    if (img->dtype != HD_U8 && img->dtype != HD_U16) return HD_ERR_DTYPE;
+    if (img->dtype == HD_U8 && img->p.bits != 8) return HD_ERR_DTYPE;
+    if (img->dtype == HD_U16 && (img->p.bits < 1 || img->p.bits > 16)) return HD_ERR_DTYPE;
+    if (img->H < 1 || img->W < 1) return HD_ERR_ARG;
+    if (img->H > HD_DIM_MAX || img->W > HD_DIM_MAX) return HD_ERR_OVERFLOW;
+    if (!img->src || !img->dst) return HD_ERR_ARG;
+    const size_t es = (size_t)elem_size(img->dtype);
+    const size_t row = (size_t)img->W * es;
+    if (img->src_pitch < row || img->dst_pitch < row) return HD_ERR_ARG;
+    if (es == 2) {
+        if ((img->src_pitch | img->dst_pitch) & 1) return HD_ERR_ARG;
+        if (((uintptr_t)img->src | (uintptr_t)img->dst) & 1) return HD_ERR_ARG;
+    }
+    // the median reads only the noisy input: source and destination must not overlap
+    const uintptr_t s0 = (uintptr_t)img->src, s1 = s0 + (size_t)(img->H - 1) * img->src_pitch + row;
+    const uintptr_t d0 = (uintptr_t)img->dst, d1 = d0 + (size_t)(img->H - 1) * img->dst_pitch + row;
+    if (s0 < d1 && d0 < s1) return HD_ERR_ARG;
+    if (need_amf) {
+        const int s = img->p.smax;
+        if (s < 3 || s > HD_SMAX_MAX || (s & 1) == 0) return HD_ERR_SMAX;
+        if (img->p.unresolved != HD_UNRESOLVED_ZMED && img->p.unresolved != HD_UNRESOLVED_KEEP)
+            return HD_ERR_ARG;
+    }
+    if (need_wiener) {
+        const int w = img->p.wiener_w;
+        if (w < 1 || w > HD_WIENER_W_MAX || (w & 1) == 0) return HD_ERR_WINDOW;
+        if (img->p.border != HD_BORDER_SYMMETRIC && img->p.border != HD_BORDER_ZERO) return HD_ERR_ARG;
+        if (!(img->p.noise_var == img->p.noise_var)) return HD_ERR_ARG;   // NaN
+        if (img->y_out && ((uintptr_t)img->y_out & 3)) return HD_ERR_ARG;
+        if (img->noise_var_out && ((uintptr_t)img->noise_var_out & 7)) return HD_ERR_ARG;
+    }
+    (void)host_buffers;
+    return HD_OK;
+}
+
+int device_sms()
+{
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (cache[dev] == 0) cache[dev] = sm_count();
+    return cache[dev];
+}
+
+size_t f_pitch_of(int W, int dtype) { return round_up((size_t)W * elem_size(dtype), 16); }
+
+// Workspace layout of a single image: [ticket][ImgCtl] [fbuf]
+size_t ctl_bytes() { return round_up(kTicketBytes + sizeof(ImgCtl), kAlign); }
+
+size_t single_ws_bytes(int H, int W, int dtype, bool needs_fbuf)
+{
+    size_t b = ctl_bytes();
+    if (needs_fbuf) b += round_up((size_t)H * f_pitch_of(W, dtype), kAlign);
+    return b;
+}
+
+ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl, uint8_t *fbuf)
+{
+    ImgDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.src = static_cast<const uint8_t *>(img->src);
+    d.dst = static_cast<uint8_t *>(img->dst);
+    d.fbuf = fbuf;
+    d.src_pitch = (long long)img->src_pitch;
+    d.dst_pitch = (long long)img->dst_pitch;
+    d.f_pitch = (long long)f_pitch_of(img->W, img->dtype);
+    d.noise_var = img->p.noise_var;
+    d.noise_var_out = img->noise_var_out;
+    d.y_out = img->y_out;
+    d.ctl = ctl;
+    d.H = img->H;
+    d.W = img->W;
+    d.elem = elem_size(img->dtype);
+    d.maxv = (int)((1u << img->p.bits) - 1u);
+    d.smax = img->p.smax;
+    d.w = img->p.wiener_w;
+    d.unresolved = img->p.unresolved;
+    d.border_zero = img->p.border == HD_BORDER_ZERO;
+    d.mode = mode;
+    d.tiles_x = (img->W + t.tile_w - 1) / t.tile_w;
+    d.tiles_y = (img->H + t.tile_h - 1) / t.tile_h;
+    return d;
+}
+
+int halo_a(const ImgDesc &d) { return (d.mode == MODE_AMF || d.mode == MODE_HYBRID_EST || d.mode == MODE_HYBRID_GIVEN) ? d.smax / 2 : 0; }
+int halo_w(const ImgDesc &d) { return d.mode == MODE_AMF ? 0 : d.w / 2; }
+
+hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t *smem)
+{
+    lp.tile_w = t.tile_w;
+    lp.tile_h = t.tile_h;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        lp.spin_limit = g_spin_limit;
+    }
+    *smem = smem_bytes(t.tile_w, t.tile_h, lp.ra_max, lp.rw_max);
+    if (*smem > 227 * 1024) return HD_ERR_OVERFLOW;
+    const int sms = device_sms();
+    if (sms <= 0) return HD_ERR_CUDA;
+    int per_sm = max_ctas_per_sm(*smem);
+    if (per_sm <= 0) return HD_ERR_CUDA;
+    if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
+    *grid = std::max(1, std::min(lp.total_items, sms * per_sm));
+    return HD_OK;
+}
+
+// Launch one image.  ws may be null for single-phase modes without a queue.
+hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    const hd_tuning t = current_tuning();
+    const bool two_phase = mode == MODE_WIENER_EST || mode == MODE_HYBRID_EST;
+    const bool needs_fbuf = mode == MODE_HYBRID_EST;
+    ImgCtl *ctl = nullptr;
+    unsigned int *ticket = nullptr;
+    uint8_t *fbuf = nullptr;
+    if (two_phase) {
+        if (!ws || ((uintptr_t)ws % kAlign)) return HD_ERR_WORKSPACE;
+        if (ws_bytes < single_ws_bytes(img->H, img->W, img->dtype, needs_fbuf)) return HD_ERR_WORKSPACE;
+        ticket = static_cast<unsigned int *>(ws);
+        ctl = reinterpret_cast<ImgCtl *>(static_cast<uint8_t *>(ws) + kTicketBytes);
+        if (needs_fbuf) fbuf = static_cast<uint8_t *>(ws) + ctl_bytes();
+    }
+    LaunchParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.descs = nullptr;
+    lp.segs = nullptr;
+    lp.one = make_desc(img, mode, t, ctl, fbuf);
+    const int tiles = lp.one.tiles_x * lp.one.tiles_y;
+    lp.oneseg[0] = Seg{0, 1, 0, tiles};
+    lp.nsegs = 1;
+    lp.total_items = tiles;
+    if (two_phase) {
+        lp.oneseg[1] = Seg{0, 2, tiles, tiles};
+        lp.nsegs = 2;
+        lp.total_items = 2 * tiles;
+        lp.ticket = ticket;
+        lp.ctl_reset = ctl;
+        lp.nctl = 1;
+    }
+    lp.ra_max = halo_a(lp.one);
+    lp.rw_max = halo_w(lp.one);
+    int grid = 0;
+    size_t smem = 0;
+    hd_status st = finish_params(lp, t, &grid, &smem);
+    if (st != HD_OK) return st;
+    if (launch_persistent(lp, grid, smem, (void *)s) != 0) return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+int hybrid_mode(const hd_image *img) { return img->p.noise_var < 0.0 ? MODE_HYBRID_EST : MODE_HYBRID_GIVEN; }
+
+// ---------------------------------------------------------------- batches
+struct BatchLayout {
+    size_t ctl_off, desc_off, seg_off, fbuf_off, total;
+    std::vector<size_t> fbuf_offsets;   // per image, or SIZE_MAX when not needed
+};
+
+BatchLayout batch_layout(const hd_image *imgs, int n)
+{
+    BatchLayout L;
+    size_t off = kTicketBytes;
+    L.ctl_off = off;
+    off = round_up(off + sizeof(ImgCtl) * (size_t)n, kAlign);
+    L.desc_off = off;
+    off = round_up(off + sizeof(ImgDesc) * (size_t)n, kAlign);
+    L.seg_off = off;
+    off = round_up(off + sizeof(Seg) * (size_t)(2 * n), kAlign);
+    L.fbuf_off = off;
+    L.fbuf_offsets.resize(n);
+    for (int i = 0; i < n; ++i) {
+        if (hybrid_mode(&imgs[i]) == MODE_HYBRID_EST) {
+            L.fbuf_offsets[i] = off;
+            off += round_up((size_t)imgs[i].H * f_pitch_of(imgs[i].W, imgs[i].dtype), kAlign);
+        } else {
+            L.fbuf_offsets[i] = SIZE_MAX;
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+struct BatchTables {
+    std::vector<ImgDesc> descs;
+    std::vector<Seg> segs;
+    int total_items = 0;
+    int ra_max = 0, rw_max = 0;
+    size_t table_bytes = 0;   // bytes from ctl_off to the end of the segment table
+};
+
+hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, BatchTables &bt,
+                      BatchLayout &L)
+{
+    if (!imgs || n < 1) return HD_ERR_ARG;
+    if (n > (1 << 20)) return HD_ERR_OVERFLOW;
+    for (int i = 0; i < n; ++i) {
+        hd_status st = check_image(&imgs[i], true, true, false);
+        if (st != HD_OK) return st;
+    }
+    L = batch_layout(imgs, n);
+    if (!ws || ((uintptr_t)ws % kAlign)) return HD_ERR_WORKSPACE;
+    if (ws_bytes < L.total) return HD_ERR_WORKSPACE;
+    const hd_tuning t = current_tuning();
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    ImgCtl *ctl = reinterpret_cast<ImgCtl *>(base + L.ctl_off);
+    bt.descs.resize(n);
+    for (int i = 0; i < n; ++i) {
+        uint8_t *fb = L.fbuf_offsets[i] == SIZE_MAX ? nullptr : base + L.fbuf_offsets[i];
+        bt.descs[i] = make_desc(&imgs[i], hybrid_mode(&imgs[i]), t, ctl + i, fb);
+        bt.ra_max = std::max(bt.ra_max, halo_a(bt.descs[i]));
+        bt.rw_max = std::max(bt.rw_max, halo_w(bt.descs[i]));
+    }
+    // ticket order: P1(0), P1(1), P2(0), P1(2), P2(1), ..., P2(n-1).  An image's
+    // Wiener tiles follow its median tiles with one image of lag, so they seldom wait.
+    long long first = 0;
+    auto push = [&](int img, int phase) {
+        const int tiles = bt.descs[img].tiles_x * bt.descs[img].tiles_y;
+        bt.segs.push_back(Seg{img, phase, (int)first, tiles});
+        first += tiles;
+    };
+    for (int i = 0; i < n; ++i) {
+        push(i, 1);
+        if (i >= 1 && mode_two_phase(bt.descs[i - 1].mode)) push(i - 1, 2);
+    }
+    if (mode_two_phase(bt.descs[n - 1].mode)) push(n - 1, 2);
+    if (first > 0x7fffffffLL) return HD_ERR_OVERFLOW;
+    bt.total_items = (int)first;
+    bt.table_bytes = L.seg_off + sizeof(Seg) * bt.segs.size() - L.ctl_off;
+    return HD_OK;
+}
+
+LaunchParams batch_params(void *ws, const BatchLayout &L, const BatchTables &bt)
+{
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    LaunchParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.descs = reinterpret_cast<const ImgDesc *>(base + L.desc_off);
+    lp.segs = reinterpret_cast<const Seg *>(base + L.seg_off);
+    lp.nsegs = (int)bt.segs.size();
+    lp.total_items = bt.total_items;
+    lp.ticket = reinterpret_cast<unsigned int *>(base);
+    lp.ctl_reset = reinterpret_cast<ImgCtl *>(base + L.ctl_off);
+    lp.nctl = (int)bt.descs.size();
+    lp.ra_max = bt.ra_max;
+    lp.rw_max = bt.rw_max;
+    return lp;
+}
+
+// Host image of the descriptor + segment tables, laid out as in the workspace.
+std::vector<uint8_t> table_image(const BatchLayout &L, const BatchTables &bt)
+{
+    std::vector<uint8_t> h(L.seg_off + sizeof(Seg) * bt.segs.size() - L.desc_off, 0);
+    std::memcpy(h.data(), bt.descs.data(), sizeof(ImgDesc) * bt.descs.size());
+    std::memcpy(h.data() + (L.seg_off - L.desc_off), bt.segs.data(), sizeof(Seg) * bt.segs.size());
+    return h;
+}
+
+}  // namespace
+
+struct hd_batch_plan {
+    void *ws = nullptr;
+    LaunchParams lp;
+    int grid = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+hd_status amf_filter(const hd_image *img, hd_stream_t stream)
+{
+    hd_status st = check_image(img, true, false, false);
+    if (st != HD_OK) return st;
+    return run_single(img, MODE_AMF, nullptr, 0, (cudaStream_t)stream);
+}
+
+hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes)
+{
+    if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
+    if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;
+    *bytes = p->noise_var < 0.0 ? single_ws_bytes(H, W, dtype, false) : 0;
+    return HD_OK;
+}
+
+hd_status wiener_filter(const hd_image *img, void *workspace, size_t ws_bytes, hd_stream_t stream)
+{
+    hd_status st = check_image(img, false, true, false);
+    if (st != HD_OK) return st;
+    const int mode = img->p.noise_var < 0.0 ? MODE_WIENER_EST : MODE_WIENER_GIVEN;
+    return run_single(img, mode, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes)
+{
+    if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
+    if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;
+    *bytes = p->noise_var < 0.0 ? single_ws_bytes(H, W, dtype, true) : 0;
+    return HD_OK;
+}
+
+hd_status hybrid_denoise(const hd_image *img, void *workspace, size_t ws_bytes, hd_stream_t stream)
+{
+    hd_status st = check_image(img, true, true, false);
+    if (st != HD_OK) return st;
+    return run_single(img, hybrid_mode(img), workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes)
+{
+    size_t b = 0;
+    hd_status st = hybrid_workspace_size(H, W, dtype, p, &b);
+    if (st != HD_OK) return st;
+    const size_t plane = round_up((size_t)H * f_pitch_of(W, dtype), kAlign);
+    *bytes = round_up(b, kAlign) + 2 * plane;
+    return HD_OK;
+}
+
+hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_bytes, hd_stream_t stream)
+{
+    hd_status st = check_image(img, true, true, true);
+    if (st != HD_OK) return st;
+    size_t need = 0;
+    hybrid_host_workspace_size(img->H, img->W, img->dtype, &img->p, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return HD_ERR_WORKSPACE;
+    if (ws_bytes < need) return HD_ERR_WORKSPACE;
+    size_t core = 0;
+    hybrid_workspace_size(img->H, img->W, img->dtype, &img->p, &core);
+    core = round_up(core, kAlign);
+    const size_t pitch = f_pitch_of(img->W, img->dtype);
+    const size_t plane = round_up((size_t)img->H * pitch, kAlign);
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    uint8_t *dsrc = base + core;
+    uint8_t *ddst = dsrc + plane;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t row = (size_t)img->W * elem_size(img->dtype);
+    if (cudaMemcpy2DAsync(dsrc, pitch, img->src, img->src_pitch, row, img->H, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    hd_image dimg = *img;
+    dimg.src = dsrc;
+    dimg.dst = ddst;
+    dimg.src_pitch = pitch;
+    dimg.dst_pitch = pitch;
+    st = run_single(&dimg, hybrid_mode(&dimg), core ? workspace : nullptr, core, s);
+    if (st != HD_OK) return st;
+    if (cudaMemcpy2DAsync(img->dst, img->dst_pitch, ddst, pitch, row, img->H, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+hd_status hybrid_batched_workspace_size(const hd_image *imgs, int n, size_t *bytes)
+{
+    if (!imgs || n < 1 || !bytes) return HD_ERR_ARG;
+    *bytes = batch_layout(imgs, n).total;
+    return HD_OK;
+}
+
+hd_status hybrid_denoise_batched(const hd_image *imgs, int n, void *workspace, size_t ws_bytes,
+                                 hd_stream_t stream)
+{
+    BatchTables bt;
+    BatchLayout L;
+    hd_status st = build_batch(imgs, n, workspace, ws_bytes, bt, L);
+    if (st != HD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint8_t> h = table_image(L, bt);
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    if (cudaMemcpyAsync(base + L.desc_off, h.data(), h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return HD_ERR_CUDA;
+    if (cudaMemsetAsync(base, 0, L.desc_off, s) != cudaSuccess) return HD_ERR_CUDA;
+    LaunchParams lp = batch_params(workspace, L, bt);
+    int grid = 0;
+    size_t smem = 0;
+    st = finish_params(lp, current_tuning(), &grid, &smem);
+    if (st != HD_OK) return st;
+    // a copy from pageable memory has consumed `h` when cudaMemcpyAsync returns
+    if (launch_persistent(lp, grid, smem, (void *)s) != 0) return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+hd_status hd_batch_plan_create(const hd_image *imgs, int n, void *workspace, size_t ws_bytes,
+                               hd_batch_plan **plan)
+{
+    if (!plan) return HD_ERR_ARG;
+    *plan = nullptr;
+    BatchTables bt;
+    BatchLayout L;
+    hd_status st = build_batch(imgs, n, workspace, ws_bytes, bt, L);
+    if (st != HD_OK) return st;
+    std::vector<uint8_t> h = table_image(L, bt);
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    if (cudaMemcpy(base + L.desc_off, h.data(), h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return HD_ERR_CUDA;
+    if (cudaMemset(base, 0, L.desc_off) != cudaSuccess) return HD_ERR_CUDA;
+    hd_batch_plan *p = new (std::nothrow) hd_batch_plan();
+    if (!p) return HD_ERR_ARG;
+    p->ws = workspace;
+    p->lp = batch_params(workspace, L, bt);
+    st = finish_params(p->lp, current_tuning(), &p->grid, &p->smem);
+    if (st != HD_OK) {
+        delete p;
+        return st;
+    }
+    // record the kernel as a graph on a private capture stream
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        delete p;
+        return HD_ERR_CUDA;
+    }
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) ok = launch_persistent(p->lp, p->grid, p->smem, (void *)cs) == 0;
+    cudaGraph_t g = nullptr;
+    const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+    ok = ok && ended && g;
+    if (ok) ok = cudaGraphInstantiate(&p->exec, g, 0) == cudaSuccess;
+    cudaStreamDestroy(cs);
+    p->graph = g;
+    if (!ok) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        delete p;
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
+    *plan = p;
+    return HD_OK;
+}
+
+hd_status hd_batch_plan_launch(hd_batch_plan *plan, hd_stream_t stream)
+{
+    if (!plan || !plan->exec) return HD_ERR_ARG;
+    if (cudaGraphLaunch(plan->exec, (cudaStream_t)stream) != cudaSuccess) return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+hd_status hd_batch_plan_destroy(hd_batch_plan *plan)
+{
+    if (!plan) return HD_ERR_ARG;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+    return HD_OK;
+}
+
+hd_status hd_set_tuning(const hd_tuning *t)
+{
+    if (!t) return HD_ERR_ARG;
+    if (t->tile_w < 8 || t->tile_w > 256 || (t->tile_w % 8) != 0) return HD_ERR_ARG;
+    if (t->tile_h < 4 || t->tile_h > 128) return HD_ERR_ARG;
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 8) return HD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = *t;
+    return HD_OK;
+}
+
+hd_status hd_get_tuning(hd_tuning *t)
+{
+    if (!t) return HD_ERR_ARG;
+    *t = current_tuning();
+    return HD_OK;
+}
+
+hd_status hd_set_spin_limit(unsigned long long polls)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_spin_limit = polls ? polls : kSpinLimit;
+    return HD_OK;
+}
+
+hd_status hd_get_device_error(hd_stream_t stream)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return HD_ERR_CUDA;
+    unsigned int v = 0;
+    if (read_and_clear_device_error(&v) != 0) return HD_ERR_CUDA;
+    if (v & DEVERR_TIMEOUT) return HD_ERR_TIMEOUT;
+    return HD_OK;
+}
+
+const char *hd_status_str(hd_status s)
+{
+    switch (s) {
+    case HD_OK: return "ok";
+    case HD_ERR_ARG: return "invalid argument";
+    case HD_ERR_SMAX: return "Smax must be an odd integer in [3, HD_SMAX_MAX]";
+    case HD_ERR_WINDOW: return "Wiener window must be an odd integer in [1, HD_WIENER_W_MAX]";
+    case HD_ERR_DTYPE: return "unsupported dtype or bit depth";
+    case HD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case HD_ERR_CUDA: return "CUDA runtime error";
+    case HD_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case HD_ERR_OVERFLOW: return "size beyond library limits";
+    }
+    return "unknown status";
+}
+
+int hd_version(void) { return 100; }
+
+}  // extern "C"

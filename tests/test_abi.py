@@ -1,0 +1,132 @@
+"""The C-ABI library loads, exports every declared symbol, and validates
+arguments on the host before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests._lib import ROOT, ensure_built
+
+ensure_built()
+import paper_2005_05371_gb300 as hd  # noqa: E402
+
+HEADER = os.path.join(ROOT, "include", "hybrid_denoise.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    assert set(hd.EXPORTS) == set(names), set(hd.EXPORTS) ^ set(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(hd.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version():
+    assert hd.hd_status_str(hd.HD_OK) == "ok"
+    assert "Smax" in hd.hd_status_str(hd.HD_ERR_SMAX)
+    assert hd.hd_status_str(99) == "unknown status"
+    assert hd.hd_version() >= 100
+
+
+def _img(H=16, W=16, dtype=hd.HD_U8, smax=5, w=3, bits=None, src=0x100000, dst=0x900000,
+         pitch=None, noise_var=-1.0, border=0, unresolved=0):
+    es = 1 if dtype == hd.HD_U8 else 2
+    pitch = pitch if pitch is not None else W * es
+    b = bits if bits is not None else (8 if dtype == hd.HD_U8 else 12)
+    p = hd.hd_params(smax, w, noise_var, border, unresolved, b)
+    return hd.hd_image(src, dst, H, W, pitch, pitch, dtype, p, None, None)
+
+
+def call(fn, img, ws=None, nbytes=0):
+    lib = hd._lib
+    if fn == "amf_filter":
+        return lib.amf_filter(ctypes.byref(img), None)
+    return getattr(lib, fn)(ctypes.byref(img), ws, nbytes, None)
+
+
+@pytest.mark.parametrize("fn", ["amf_filter", "hybrid_denoise"])
+@pytest.mark.parametrize("smax", [-1, 0, 1, 2, 4, 10, 17, 101])
+def test_smax_rejected(fn, smax):
+    # Algorithm 1, step 6a: Smax must be an odd integer > 1 (and within the build's cap)
+    assert call(fn, _img(smax=smax)) == hd.HD_ERR_SMAX
+
+
+@pytest.mark.parametrize("w", [0, -1, 2, 4, 17])
+def test_window_rejected(w):
+    assert call("wiener_filter", _img(w=w)) == hd.HD_ERR_WINDOW
+    assert call("hybrid_denoise", _img(w=w)) == hd.HD_ERR_WINDOW
+
+
+def test_bad_arguments_rejected():
+    assert call("amf_filter", _img(src=0)) == hd.HD_ERR_ARG
+    assert call("amf_filter", _img(dst=0)) == hd.HD_ERR_ARG
+    assert call("amf_filter", _img(H=0)) == hd.HD_ERR_ARG
+    assert call("amf_filter", _img(W=-3)) == hd.HD_ERR_ARG
+    assert call("amf_filter", _img(H=70000)) == hd.HD_ERR_OVERFLOW
+    assert call("amf_filter", _img(pitch=15)) == hd.HD_ERR_ARG               # pitch < W
+    assert call("amf_filter", _img(dtype=hd.HD_U16, pitch=33)) == hd.HD_ERR_ARG   # odd pitch
+    assert call("amf_filter", _img(dtype=7)) == hd.HD_ERR_DTYPE
+    assert call("amf_filter", _img(dtype=hd.HD_U8, bits=12)) == hd.HD_ERR_DTYPE
+    assert call("amf_filter", _img(dtype=hd.HD_U16, bits=17)) == hd.HD_ERR_DTYPE
+    assert call("amf_filter", _img(dtype=hd.HD_U16, bits=0)) == hd.HD_ERR_DTYPE
+    assert call("amf_filter", _img(unresolved=5)) == hd.HD_ERR_ARG
+    assert call("wiener_filter", _img(border=3)) == hd.HD_ERR_ARG
+    assert call("wiener_filter", _img(noise_var=float("nan"))) == hd.HD_ERR_ARG
+    # source and destination overlap
+    assert call("amf_filter", _img(src=0x100000, dst=0x100000 + 40)) == hd.HD_ERR_ARG
+
+
+def test_workspace_checks_before_launch():
+    img = _img()
+    assert call("hybrid_denoise", img, None, 0) == hd.HD_ERR_WORKSPACE
+    assert call("hybrid_denoise", img, 0x1000 + 8, 1 << 20) == hd.HD_ERR_WORKSPACE   # misaligned
+    need = hd.hybrid_workspace_size(16, 16, hd.HD_U8, hd.Params(5, 3))
+    assert call("hybrid_denoise", img, 0x10000, need - 1) == hd.HD_ERR_WORKSPACE
+
+
+def test_workspace_sizes():
+    p = hd.Params(11, 5)
+    n8 = hd.hybrid_workspace_size(1620, 1620, hd.HD_U8, p)
+    n16 = hd.hybrid_workspace_size(4096, 4096, hd.HD_U16, p)
+    assert n8 >= 1620 * 1620 and n8 < 1620 * 1620 + 64 * 1024
+    assert n16 >= 4096 * 4096 * 2 and n16 < 4096 * 4096 * 2 + 64 * 1024
+    # a supplied noise variance makes the hybrid one pass: no workspace
+    assert hd.hybrid_workspace_size(512, 512, hd.HD_U8, hd.Params(7, 3, noise_var=25.0)) == 0
+    assert hd.wiener_workspace_size(512, 512, hd.HD_U8, hd.Params(7, 3)) > 0
+    assert hd.hybrid_host_workspace_size(100, 100, hd.HD_U16, p) >= 2 * 100 * 100 * 2
+
+
+def test_tuning_validation():
+    old = hd.hd_get_tuning()
+    try:
+        with pytest.raises(hd.HDError):
+            hd.hd_set_tuning(7, 32)
+        with pytest.raises(hd.HDError):
+            hd.hd_set_tuning(64, 2)
+        with pytest.raises(hd.HDError):
+            hd.hd_set_tuning(64, 32, 9)
+        hd.hd_set_tuning(32, 16, 2)
+        assert hd.hd_get_tuning() == (32, 16, 2)
+    finally:
+        hd.hd_set_tuning(*old)
+
+
+def test_batched_validation():
+    imgs = (hd.hd_image * 2)(_img(), _img(smax=4))
+    n = ctypes.c_size_t()
+    assert hd._lib.hybrid_batched_workspace_size(imgs, 0, ctypes.byref(n)) == hd.HD_ERR_ARG
+    assert hd._lib.hybrid_denoise_batched(imgs, 2, 0x10000, 1 << 30, None) == hd.HD_ERR_SMAX
+    plan = ctypes.c_void_p()
+    assert hd._lib.hd_batch_plan_create(imgs, 2, 0x10000, 1 << 30, ctypes.byref(plan)) == hd.HD_ERR_SMAX
+    assert hd._lib.hd_batch_plan_launch(None, None) == hd.HD_ERR_ARG
