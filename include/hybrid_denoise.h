@@ -164,14 +164,16 @@ hd_status hd_batch_plan_launch(hd_batch_plan *plan, hd_stream_t stream);
 hd_status hd_batch_plan_destroy(hd_batch_plan *plan);
 
 /* ---------------------------------------------------------------- tuning
- * Tile shape of the persistent kernel (output pixels per work item) and the
- * grid size in CTAs per SM.  tile_w: multiple of 8 in [8, 256]; tile_h in
- * [4, 128]; ctas_per_sm in [1, 8] (0 = as many as fit).  Applies to later
- * launches in this process. */
+ * Work-item shape of the persistent kernel.  Each item covers a region of
+ * 64 columns x region_h rows of the median output; its output tile is that
+ * region less the Wiener halo, (64 - 2*(w/2)) x (region_h - 2*(w/2)).
+ * region_h: multiple of 8 in [16, 128] (default 32).  ctas_per_sm: grid size
+ * per SM, 1..8, 0 = as many as fit.  reserved must be 0.  Applies to later
+ * launches in this process; results do not depend on it. */
 typedef struct {
-    int tile_w;
-    int tile_h;
+    int region_h;
     int ctas_per_sm;
+    int reserved;
 } hd_tuning;
 hd_status hd_set_tuning(const hd_tuning *t);
 hd_status hd_get_tuning(hd_tuning *t);

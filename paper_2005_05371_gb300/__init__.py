@@ -51,7 +51,7 @@ class hd_image(ctypes.Structure):
 
 
 class hd_tuning(ctypes.Structure):
-    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("region_h", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class HDError(RuntimeError):
@@ -332,15 +332,16 @@ class BatchPlan:
 
 
 # ----------------------------------------------------------------- tuning / errors
-def hd_set_tuning(tile_w: int, tile_h: int, ctas_per_sm: int = 0):
-    t = hd_tuning(tile_w, tile_h, ctas_per_sm)
+def hd_set_tuning(region_h: int = 32, ctas_per_sm: int = 0):
+    """Rows per work item (multiple of 8 in [16, 128]) and CTAs per SM (0 = all that fit)."""
+    t = hd_tuning(region_h, ctas_per_sm, 0)
     _check(_lib.hd_set_tuning(ctypes.byref(t)), "hd_set_tuning")
 
 
-def hd_get_tuning() -> tuple[int, int, int]:
+def hd_get_tuning() -> tuple[int, int]:
     t = hd_tuning()
     _check(_lib.hd_get_tuning(ctypes.byref(t)), "hd_get_tuning")
-    return t.tile_w, t.tile_h, t.ctas_per_sm
+    return t.region_h, t.ctas_per_sm
 
 
 def hd_set_spin_limit(polls: int = 0):

@@ -26,7 +26,7 @@ constexpr unsigned long long kSpinLimit = 8000000ull;   // polls of >= 256 ns: a
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 std::mutex g_tune_mu;
-hd_tuning g_tune = {64, 32, 0};
+hd_tuning g_tune = {32, 0, 0};
 unsigned long long g_spin_limit = kSpinLimit;
 
 hd_tuning current_tuning()
@@ -124,23 +124,33 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     d.unresolved = img->p.unresolved;
     d.border_zero = img->p.border == HD_BORDER_ZERO;
     d.mode = mode;
-    d.tiles_x = (img->W + t.tile_w - 1) / t.tile_w;
-    d.tiles_y = (img->H + t.tile_h - 1) / t.tile_h;
+    // same tile shape as the kernel: left margin rw rounded up to even, width even
+    const int rw = mode == MODE_AMF ? 0 : img->p.wiener_w / 2;
+    const int lm = rw + (rw & 1);
+    const int TW = (64 - lm - rw) & ~1, TH = t.region_h - 2 * rw;
+    d.tiles_x = (img->W + TW - 1) / TW;
+    d.tiles_y = (img->H + TH - 1) / TH;
     return d;
 }
 
+// Same test as the kernel: 32-bit Wiener sums are exact when n * maxv < 2^17.
+bool image_wide(const ImgDesc &d)
+{
+    if (d.mode == MODE_AMF) return false;
+    const long long n = (long long)d.w * d.w;
+    return !(d.maxv < 0x8000 && (long long)(d.w + 1) * d.maxv <= 65535 && n * d.maxv < 131072);
+}
+
 int halo_a(const ImgDesc &d) { return (d.mode == MODE_AMF || d.mode == MODE_HYBRID_EST || d.mode == MODE_HYBRID_GIVEN) ? d.smax / 2 : 0; }
-int halo_w(const ImgDesc &d) { return d.mode == MODE_AMF ? 0 : d.w / 2; }
 
 hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t *smem)
 {
-    lp.tile_w = t.tile_w;
-    lp.tile_h = t.tile_h;
+    lp.region_h = t.region_h;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         lp.spin_limit = g_spin_limit;
     }
-    *smem = smem_bytes(t.tile_w, t.tile_h, lp.ra_max, lp.rw_max);
+    *smem = smem_bytes(t.region_h, lp.ra_max, lp.wide);
     if (*smem > 227 * 1024) return HD_ERR_OVERFLOW;
     const int sms = device_sms();
     if (sms <= 0) return HD_ERR_CUDA;
@@ -185,7 +195,7 @@ hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, c
         lp.nctl = 1;
     }
     lp.ra_max = halo_a(lp.one);
-    lp.rw_max = halo_w(lp.one);
+    lp.wide = image_wide(lp.one);
     int grid = 0;
     size_t smem = 0;
     hd_status st = finish_params(lp, t, &grid, &smem);
@@ -230,7 +240,7 @@ struct BatchTables {
     std::vector<ImgDesc> descs;
     std::vector<Seg> segs;
     int total_items = 0;
-    int ra_max = 0, rw_max = 0;
+    int ra_max = 0, wide = 0;
     size_t table_bytes = 0;   // bytes from ctl_off to the end of the segment table
 };
 
@@ -254,7 +264,7 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
         uint8_t *fb = L.fbuf_offsets[i] == SIZE_MAX ? nullptr : base + L.fbuf_offsets[i];
         bt.descs[i] = make_desc(&imgs[i], hybrid_mode(&imgs[i]), t, ctl + i, fb);
         bt.ra_max = std::max(bt.ra_max, halo_a(bt.descs[i]));
-        bt.rw_max = std::max(bt.rw_max, halo_w(bt.descs[i]));
+        bt.wide |= image_wide(bt.descs[i]) ? 1 : 0;
     }
     // ticket order: P1(0), P1(1), P2(0), P1(2), P2(1), ..., P2(n-1).  An image's
     // Wiener tiles follow its median tiles with one image of lag, so they seldom wait.
@@ -288,7 +298,7 @@ LaunchParams batch_params(void *ws, const BatchLayout &L, const BatchTables &bt)
     lp.ctl_reset = reinterpret_cast<ImgCtl *>(base + L.ctl_off);
     lp.nctl = (int)bt.descs.size();
     lp.ra_max = bt.ra_max;
-    lp.rw_max = bt.rw_max;
+    lp.wide = bt.wide;
     return lp;
 }
 
@@ -494,8 +504,8 @@ hd_status hd_batch_plan_destroy(hd_batch_plan *plan)
 hd_status hd_set_tuning(const hd_tuning *t)
 {
     if (!t) return HD_ERR_ARG;
-    if (t->tile_w < 8 || t->tile_w > 256 || (t->tile_w % 8) != 0) return HD_ERR_ARG;
-    if (t->tile_h < 4 || t->tile_h > 128) return HD_ERR_ARG;
+    if (t->region_h < 16 || t->region_h > 128 || (t->region_h % 8) != 0) return HD_ERR_ARG;
+    if (t->reserved != 0) return HD_ERR_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 8) return HD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = *t;

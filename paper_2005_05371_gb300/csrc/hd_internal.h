@@ -1,7 +1,9 @@
 // hd_internal.h -- types shared by the persistent kernel and the host API.
 //
-// Work decomposition: every image is cut into output tiles of tile_w x tile_h
-// pixels.  A work item is (image, phase, tile).  Items are taken in ticket
+// Work decomposition: every image is cut into output tiles of
+// (64 - 2 Rw) x (region_h - 2 Rw) pixels, Rw = w/2 (0 for the median alone), so
+// that tile plus Wiener halo is a 64 x region_h region.  A work item is
+// (image, phase, tile).  Items are taken in ticket
 // order from one global counter by the CTAs of a persistent grid, so a CTA
 // only ever waits on items that running CTAs already hold.
 #pragma once
@@ -22,14 +24,20 @@ inline bool mode_two_phase(int m) { return m == MODE_WIENER_EST || m == MODE_HYB
 inline bool mode_has_amf(int m) { return m == MODE_AMF || m == MODE_HYBRID_EST || m == MODE_HYBRID_GIVEN; }
 inline bool mode_has_wiener(int m) { return m != MODE_AMF; }
 
-// Per-image control block in the workspace (32 bytes, zeroed before a launch).
+// Per-image control block in the workspace (64 bytes, zero between launches).
+// sum over pixels of D = n*S2 - S1^2 is n*B - A, both exact integers:
+//   A = sum over pixels p of S1_p^2,  B = sum over pixels q of M(q) f_q^2,
+// M(q) = number of (pixel, window offset) pairs whose sample is q.
+// Each tile adds the low and high 32-bit halves of its 64-bit partials to
+// separate 64-bit words (A = A_hi32 * 2^32 + A_lo32), so the adds need no
+// returned value and cannot overflow for fewer than 2^32 tiles.
 struct ImgCtl {
-    unsigned long long sumD_lo;   // sum over pixels of D = n*S2 - S1^2, low word
-    unsigned long long sumD_hi;   // carry word
+    unsigned long long A_lo32, A_hi32;
+    unsigned long long B_lo32, B_hi32;
     unsigned int p1_done;         // phase-1 tiles finished
-    unsigned int pad[3];
+    unsigned int pad[7];
 };
-static_assert(sizeof(ImgCtl) == 32, "ImgCtl layout");
+static_assert(sizeof(ImgCtl) == 64, "ImgCtl layout");
 
 struct ImgDesc {
     const uint8_t *src;
@@ -73,13 +81,14 @@ struct LaunchParams {
                               // reset to zero by the last CTA to exit
     ImgCtl *ctl_reset;        // control blocks the last CTA zeroes (nctl of them)
     int nctl;
-    int tile_w, tile_h;
-    int ra_max, rw_max;       // largest halos over the launch (shared memory sizing)
+    int region_h;             // rows of the f region: multiple of 8 in [16, 128]
+    int ra_max;               // largest median halo over the launch (shared memory sizing)
+    int wide;                 // some image needs 64-bit Wiener sums
     unsigned long long spin_limit;   // bounded wait, in polls
 };
 
-// Shared-memory bytes the kernel needs for a given tile and halos.
-size_t smem_bytes(int tile_w, int tile_h, int ra_max, int rw_max);
+// Shared-memory bytes the kernel needs.
+size_t smem_bytes(int region_h, int ra_max, int wide);
 
 // Launch the persistent kernel; returns cudaError_t as int.
 int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *stream);

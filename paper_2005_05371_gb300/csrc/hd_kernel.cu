@@ -1,34 +1,60 @@
 // hd_kernel.cu -- the persistent hybrid-denoise kernel for sm_103a.
 //
 // One launch runs a whole image (or a batch of images) through
-//   phase 1: adaptive median (Algorithm 1, step 6) on a shared-memory tile
-//            plus the Wiener halo, then the exact local statistics D of the
-//            median output and a per-image integer sum of D (the noise
-//            variance of the Wiener stage is the mean local variance);
+//   phase 1: adaptive median (Algorithm 1, step 6) over a 64-column region in
+//            shared memory (the output tile plus the Wiener halo), then the
+//            exact integer pieces of the image-wide noise variance;
 //   phase 2: Wiener apply (Algorithm 1, step 4d) once every phase-1 tile of
 //            that image is done.
 // Work items (image, phase, tile) are handed out in ticket order by one
-// global counter.  A CTA takes its next ticket only after any wait of its
-// current item is over, so every wait is on items held by running CTAs.
-// Waits are bounded: after lp.spin_limit polls the CTA latches
-// DEVERR_TIMEOUT in g_device_error and skips the item.
+// global counter.  An item only waits on items with earlier tickets, so the
+// CTA holding the earliest unfinished ticket always makes progress; a CTA may
+// therefore take its next ticket before finishing the current item.  Waits
+// are bounded: after lp.spin_limit polls the CTA latches DEVERR_TIMEOUT in
+// g_device_error and skips the item.  The last CTA to exit zeroes the queue
+// counters for the next launch.
 //
-// Median: 3x3 window statistics for every pixel from row-sorted triples
-// (median of nine = med3(max of row minima, med3 of row medians, min of row
-// maxima)); pixels failing level A join a shared-memory worklist that is
-// re-compacted for every larger window k = 5..Smax and resolved one warp per
-// pixel with a bitwise radix select over the k*k samples.
+// Region geometry.  The f region (median output the Wiener stage reads) is
+// at most 64 columns x FH rows.  Its first column is Lm = Rw rounded up to
+// an even number left of the output tile (Rw = w/2 rows above and columns
+// right), so the region starts on an even image column: pixel pairs (2i,
+// 2i+1) of the image and of shared memory line up for 32-bit accesses.  The
+// output tile is TW = (64 - Lm - Rw) rounded down to even columns by
+// FH - 2 Rw rows.  Lane l owns f columns 2l and 2l+1; each warp owns a band
+// of rows.  The noisy-input region adds the median halo Ra = Smax/2.
 //
-// Wiener: S1 = sum f and S2 = sum f^2 over w x w by separable sums in
-// shared memory, exact in 32/64-bit integers; D = n*S2 - S1^2 exact.  The gain
-// and output use binary32 with a fixed order of correctly rounded operations
-// (no contraction):
+// Median, 3x3 stage: two pixels per lane in one 32-bit word (u16x2 SIMD
+// min/max, one instruction each).  Each input row is sorted once per column
+// triple and reused by three output rows; the median of nine is med3(max of
+// row minima, med3 of row medians, min of row maxima).  Level A / level B
+// tests use packed differences (zmin <= z <= zmax lane-wise, so the
+// subtractions never borrow).  Pixels failing level A join a shared-memory
+// worklist that is re-compacted for each larger window k = 5..Smax, one thread
+// per pixel.  Level A at k needs only zmin, zmax and how often each occurs
+// (the median equals zmin exactly when zmin fills more than half the window);
+// pixels whose level B needs the median are compacted again and get it by
+// forgetful selection (k = 5, in registers) or by bisection on the value with
+// counting passes.
+//
+// Noise variance (mean local variance, exact):  sum_p D_p with
+// D_p = n*S2_p - S1_p^2 equals n * sum_q M(q) f_q^2 - sum_p S1_p^2, where M(q)
+// counts the windows (with the border rule) that contain pixel q, separable
+// into row and column counts (n for interior pixels).  Phase 1 needs only the
+// box sums S1; both sums are exact per image.
+//
+// Wiener sums: horizontal box sums H1 = sum f, H2 = sum f^2 per row (one
+// thread slides along eight columns), then vertical sliding sums per column
+// pair.  When n * maxv < 2^17 the variance numerator D < 2^32, so S2 and D
+// are computed in wrapping 32-bit arithmetic and are still exact; otherwise
+// 64-bit.  The gain and output use binary32 with a fixed order of correctly
+// rounded operations (no contraction):
 //   mu  = fl(S1) * fl(1/n)            s2 = fl(D) * fl(1/n^2)      v2 = fl(nu2)
 //   den = max(s2, v2)                 num = max(s2 - v2, 0)
 //   y   = den > 0 ? mu + (num / den) * (fl(f) - mu) : mu
 //   out = min(maxv, floor(y + 0.5))
 // nu2 = fl64( fl64(sum D) / (n*n*H*W) ) with a correctly rounded 128-bit to
-// binary64 conversion; binary64 is used only for this one scalar per image.
+// binary64 conversion, computed by one thread per CTA and image (binary64 is
+// slow on this part).
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "hd_internal.h"
@@ -37,38 +63,74 @@ namespace hd {
 
 __device__ unsigned int g_device_error;
 
+// Optional per-stage cycle counters (build with -DHD_STAGE_PROFILE): thread 0
+// of every CTA adds the clock cycles between consecutive stamps to
+// g_stage_cycles[stage].  Compiled out otherwise.
+#ifdef HD_STAGE_PROFILE
+__device__ unsigned long long g_stage_cycles[16];
+#define HD_STAMP_INIT() long long hd_t0_ = clock64()
+#define HD_STAMP(i)                                                                  \
+    do {                                                                             \
+        if (threadIdx.x == 0) {                                                      \
+            const long long t_ = clock64();                                          \
+            atomicAdd(&g_stage_cycles[i], (unsigned long long)(t_ - hd_t0_));        \
+            hd_t0_ = t_;                                                             \
+        }                                                                            \
+    } while (0)
+#else
+#define HD_STAMP_INIT() (void)0
+#define HD_STAMP(i) (void)0
+#endif
+
 namespace {
 
-struct Smem {
-    unsigned long long *V2;   // [tile_h][FWmax] vertical sums of f^2
-    unsigned int *V1;         // [tile_h][FWmax] vertical sums of f
-    unsigned int *wl0;        // worklists of (row << 16 | col) in the f region
-    unsigned int *wl1;
-    unsigned short *gs;       // noisy input region (f region + median halo)
-    unsigned short *fs;       // median output region (tile + Wiener halo)
-};
+typedef unsigned int u32;
+typedef unsigned long long u64;
+typedef unsigned short u16;
+
+constexpr int FW = 64;          // f-region width
+constexpr int FS = 66;          // f-region row stride in u16 (33 words: rows shift banks)
+constexpr int HS = 66;          // row stride of the horizontal-sum planes, in elements (even: 64-bit pairs)
+constexpr int kWarps = kThreads / 32;
+constexpr u32 FULL = 0xffffffffu;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline int g_stride(int ra) { return FW + 2 * ra + 4; }
 
 struct SmemLayout {
-    size_t v2, v1, wl0, wl1, gs, fs, total;
+    size_t fs, gs, wl, h1, h2, total;
 };
 
-__host__ __device__ inline SmemLayout layout(int tile_w, int tile_h, int ra_max, int rw_max)
+// fs is live for the whole item; the median view (gs, worklists) and the
+// Wiener view (H1, H2) share the rest.
+__host__ __device__ inline SmemLayout layout(int FH, int ra_max, int wide)
 {
-    const size_t FW = tile_w + 2 * rw_max, FH = tile_h + 2 * rw_max;
-    const size_t GW = FW + 2 * ra_max, GH = FH + 2 * ra_max;
     SmemLayout L;
-    size_t off = 0;
-    L.v2 = off;  off = align16(off + sizeof(unsigned long long) * tile_h * FW);
-    L.v1 = off;  off = align16(off + sizeof(unsigned int) * tile_h * FW);
-    L.wl0 = off; off = align16(off + sizeof(unsigned int) * FH * FW);
-    L.wl1 = off; off = align16(off + sizeof(unsigned int) * FH * FW);
-    L.gs = off;  off = align16(off + sizeof(unsigned short) * GH * GW);
-    L.fs = off;  off = align16(off + sizeof(unsigned short) * FH * FW);
-    L.total = off;
+    L.fs = 0;
+    const size_t scratch = align16((size_t)FH * FS * sizeof(u16));
+    size_t a = scratch;
+    L.gs = a;
+    a = align16(a + (size_t)(FH + 2 * ra_max) * g_stride(ra_max) * sizeof(u16));
+    L.wl = a;
+    a = align16(a + 2 * (size_t)FH * FW * sizeof(u16));
+    size_t b = scratch;
+    L.h1 = b;
+    b = align16(b + (size_t)FH * HS * sizeof(u32));
+    L.h2 = b;
+    b = align16(b + (size_t)FH * HS * (wide ? sizeof(u64) : sizeof(u32)));
+    L.total = a > b ? a : b;
     return L;
 }
+
+struct Geo {
+    int x0, y0;      // output tile origin (image coordinates)
+    int tw, th;      // output tile size (clipped at the image edge)
+    int Rw, Lm, hx;  // Wiener halo (rows above/below, columns right), left margin, Lm - Rw
+    int Ra, pa;      // median halo, column pad of the g region (Ra + pa is even)
+    int GS;          // g-region row stride (u16)
+    int ncol, nrow;  // f-region size: Lm + tw + Rw columns, th + 2 Rw rows
+    int gfx, gfy;    // image coordinates of f-region cell (0, 0)
+};
 
 // Half-sample symmetric extension with period 2n, valid for any i.
 __device__ __forceinline__ int refl(int i, int n)
@@ -80,235 +142,641 @@ __device__ __forceinline__ int refl(int i, int n)
     return m < n ? m : p - 1 - m;
 }
 
-__device__ __forceinline__ unsigned umin(unsigned a, unsigned b) { return a < b ? a : b; }
-__device__ __forceinline__ unsigned umax(unsigned a, unsigned b) { return a > b ? a : b; }
+__device__ __forceinline__ u32 umin(u32 a, u32 b) { return a < b ? a : b; }
+__device__ __forceinline__ u32 umax(u32 a, u32 b) { return a > b ? a : b; }
+__device__ __forceinline__ u32 vmin(u32 a, u32 b) { return __vminu2(a, b); }
+__device__ __forceinline__ u32 vmax(u32 a, u32 b) { return __vmaxu2(a, b); }
+__device__ __forceinline__ u32 vmed3(u32 a, u32 b, u32 c) { return vmax(vmin(a, b), vmin(vmax(a, b), c)); }
+__device__ __forceinline__ u32 smed3(u32 a, u32 b, u32 c) { return umax(umin(a, b), umin(umax(a, b), c)); }
 
-// Sort three values: on return a <= b <= c.
-__device__ __forceinline__ void sort3(unsigned &a, unsigned &b, unsigned &c)
+// ---------------------------------------------------------------- region loads / stores
+template <typename T>
+__device__ __forceinline__ T ldg_any(const T *p, bool cg)
 {
-    unsigned lo = umin(a, b), hi = umax(a, b);
-    unsigned lo2 = umin(lo, c), t = umax(lo, c);
-    a = lo2;
-    b = umin(hi, t);
-    c = umax(hi, t);
+    return cg ? __ldcg(p) : __ldg(p);
 }
 
-__device__ __forceinline__ unsigned med3(unsigned a, unsigned b, unsigned c)
+// Bytes [lo, hi) of the aligned 16-byte block at blk, by aligned pieces, into
+// q0 (bytes 0..7) and q1 (bytes 8..15); nothing outside [lo, hi) is read.
+__device__ __forceinline__ void load_partial(const uint8_t *blk, int lo, int hi, bool cg, u64 &q0, u64 &q1)
 {
-    return umax(umin(a, b), umin(umax(a, b), c));
-}
-
-__device__ __forceinline__ unsigned load_px(const uint8_t *base, long long pitch, int elem, int y, int x,
-                                            bool cg)
-{
-    const uint8_t *row = base + (long long)y * pitch;
-    if (elem == 1) return cg ? (unsigned)__ldcg(row + x) : (unsigned)row[x];
-    const unsigned short *r16 = reinterpret_cast<const unsigned short *>(row);
-    return cg ? (unsigned)__ldcg(r16 + x) : (unsigned)r16[x];
-}
-
-// Copy image rows [y0, y0+SH) x cols [x0, x0+SW) into shared memory (stride
-// SW), reflecting out-of-range indices or reading zeros there.
-__device__ void load_region(unsigned short *dst, int SW, int SH, const uint8_t *base, long long pitch,
-                            int elem, int H, int W, int y0, int x0, bool zero_outside, bool cg)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int ry = warp; ry < SH; ry += kThreads / 32) {
-        const int gy = y0 + ry;
-        const bool yout = (unsigned)gy >= (unsigned)H;
-        const int sy = refl(gy, H);
-        for (int rx = lane; rx < SW; rx += 32) {
-            const int gx = x0 + rx;
-            unsigned v;
-            if (zero_outside && (yout || (unsigned)gx >= (unsigned)W)) v = 0;
-            else v = load_px(base, pitch, elem, sy, refl(gx, W), cg);
-            dst[ry * SW + rx] = (unsigned short)v;
+    q0 = 0;
+    q1 = 0;
+    while (lo < hi) {
+        u64 v;
+        int s;
+        if ((lo & 7) == 0 && lo + 8 <= hi) {
+            v = ldg_any(reinterpret_cast<const unsigned long long *>(blk + lo), cg);
+            s = 8;
+        } else if ((lo & 3) == 0 && lo + 4 <= hi) {
+            v = ldg_any(reinterpret_cast<const unsigned int *>(blk + lo), cg);
+            s = 4;
+        } else if ((lo & 1) == 0 && lo + 2 <= hi) {
+            v = ldg_any(reinterpret_cast<const unsigned short *>(blk + lo), cg);
+            s = 2;
+        } else {
+            v = ldg_any(blk + lo, cg);
+            s = 1;
         }
+        if (lo < 8) q0 |= v << (8 * lo);
+        else q1 |= v << (8 * (lo - 8));
+        lo += s;
     }
 }
 
-struct WinStats {
-    unsigned zmin, zmed, zmax;
-};
-
-// Order statistics of the k x k window centred at c (stride GW), one warp.
-// The median is the (k*k-1)/2-th smallest sample, found bit by bit from the
-// most significant bit where zmin and zmax differ.
-__device__ WinStats warp_window_stats(const unsigned short *c, int GW, int k, int lane)
+// Fill a rows x cols shared-memory region (row stride ds u16, first column
+// at dst) with the image region whose top-left pixel is (gy0, gx0), gx0 even.
+// Rows are read from refl(gy) (or are zero outside, zero_outside); columns
+// outside the image are reflected from the loaded columns of the same row (or
+// zero).  Global reads use 16-byte vectors where a whole aligned block lies
+// inside the row, aligned narrower pieces at the two ends, and never touch a
+// byte outside the image rows.  Whole blocks whose first pixel lands on a
+// 4-byte aligned shared address go to shared memory as 32-bit pixel pairs.
+__device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t *base, long long pitch, int es,
+                            int H, int W, int gy0, int gx0, bool zero_outside, bool cg)
 {
-    const int r = k >> 1, cnt = k * k;
-    const int nslots = (cnt + 31) >> 5;      // <= 8 for k <= 15
-    unsigned v[8];
-    unsigned lmin = 0xffffffffu, lmax = 0u;
+    const int xa = max(gx0, 0), xb = min(gx0 + cols, W);   // in-image columns, xa < xb
+    const int J = ((xb - xa) * es + 15) / 16 + 1;          // blocks that can hold a row's bytes
+    const int jobs = rows * J;
+    constexpr int U = 2;
+    for (int j0 = threadIdx.x; j0 < jobs; j0 += kThreads * U) {
+        uint4 v[U];
+        int lo[U], hi[U], row[U];
+        long long xblk[U];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        unsigned x = 0xffffffffu;
-        const int j = lane + 32 * s;
-        if (s < nslots && j < cnt) {
-            const int q = j / k;
-            x = c[(q - r) * GW + (j - q * k - r)];
-            lmin = umin(lmin, x);
-            lmax = umax(lmax, x);
-        }
-        v[s] = x;
-    }
-    const unsigned zmin = __reduce_min_sync(0xffffffffu, lmin);
-    const unsigned zmax = __reduce_max_sync(0xffffffffu, lmax);
-    const unsigned diff = zmin ^ zmax;
-    if (diff == 0) return {zmin, zmin, zmax};
-    const int hb = 31 - __clz(diff);
-    unsigned prefix = zmin & ~((2u << hb) - 1u);
-    unsigned rank = (unsigned)(cnt - 1) >> 1;
-    for (int b = hb; b >= 0; --b) {
-        unsigned c0 = 0;
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            if (s < nslots) c0 += ((v[s] ^ prefix) >> b) == 0u;
-        c0 = __reduce_add_sync(0xffffffffu, c0);
-        if (rank >= c0) {
-            rank -= c0;
-            prefix |= 1u << b;
-        }
-    }
-    return {zmin, prefix, zmax};
-}
-
-// Adaptive median over the f region (FW x FH) from the g region (stride GW,
-// origin Ra rows/cols before the f region).  Writes fs.
-__device__ void amf_region(const ImgDesc &d, const Smem &sm, int FW, int FH, int GW, int Ra, int *s_cnt)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int smax = d.smax;
-    const bool keep = d.unresolved != 0;
-    // --- k = 3 for every pixel
-    for (int ry = warp; ry < FH; ry += kThreads / 32) {
-        const unsigned short *grow = sm.gs + (ry + Ra) * GW + Ra;
-        for (int rx0 = 0; rx0 < FW; rx0 += 32) {
-            const int rx = rx0 + lane;
-            bool grow_it = false;
-            if (rx < FW) {
-                const unsigned short *c = grow + rx;
-                unsigned a0 = c[-GW - 1], a1 = c[-GW], a2 = c[-GW + 1];
-                unsigned b0 = c[-1], b1 = c[0], b2 = c[1];
-                unsigned e0 = c[GW - 1], e1 = c[GW], e2 = c[GW + 1];
-                const unsigned zxy = b1;
-                sort3(a0, a1, a2);
-                sort3(b0, b1, b2);
-                sort3(e0, e1, e2);
-                const unsigned zmin = umin(umin(a0, b0), e0);
-                const unsigned zmax = umax(umax(a2, b2), e2);
-                const unsigned zmed = med3(umax(umax(a0, b0), e0), med3(a1, b1, e1),
-                                           umin(umin(a2, b2), e2));
-                unsigned out;
-                if (zmin < zmed && zmed < zmax) {                  // level A
-                    out = (zmin < zxy && zxy < zmax) ? zxy : zmed;  // level B
-                } else if (smax == 3) {
-                    out = keep ? zxy : zmed;
+        for (int u = 0; u < U; ++u) {
+            const int job = j0 + u * kThreads;
+            lo[u] = 0;
+            hi[u] = 0;
+            row[u] = 0;
+            xblk[u] = 0;
+            v[u] = make_uint4(0, 0, 0, 0);
+            if (job < jobs) {
+                const int r = job / J, bi = job - r * J;
+                row[u] = r;
+                const int gy = gy0 + r;
+                if (zero_outside && (unsigned)gy >= (unsigned)H) continue;
+                const uint8_t *rp = base + (long long)refl(gy, H) * pitch;
+                const uint8_t *a = rp + (long long)xa * es;
+                const uint8_t *b = rp + (long long)xb * es;
+                const uint8_t *blk = reinterpret_cast<const uint8_t *>(
+                    (reinterpret_cast<uintptr_t>(a) & ~uintptr_t(15)) + 16 * (uintptr_t)bi);
+                if (blk >= b) continue;
+                const int l = blk < a ? (int)(a - blk) : 0;
+                const int h = blk + 16 > b ? (int)(b - blk) : 16;
+                lo[u] = l;
+                hi[u] = h;
+                xblk[u] = (long long)(blk - rp);    // byte offset of the block within the row
+                if (l == 0 && h == 16) {
+                    v[u] = ldg_any(reinterpret_cast<const uint4 *>(blk), cg);
                 } else {
-                    out = zmed;
-                    grow_it = true;
+                    u64 q0, q1;
+                    load_partial(blk, l, h, cg, q0, q1);
+                    v[u] = make_uint4((u32)q0, (u32)(q0 >> 32), (u32)q1, (u32)(q1 >> 32));
                 }
-                sm.fs[ry * FW + rx] = (unsigned short)out;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, grow_it);
-            if (bal) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s_cnt[0], __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (grow_it)
-                    sm.wl0[base + __popc(bal & ((1u << lane) - 1u))] = ((unsigned)ry << 16) | (unsigned)rx;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (lo[u] >= hi[u]) continue;
+            u16 *drow = dst + row[u] * ds;
+            const u32 wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+            if (es == 1) {
+                const int x = (int)xblk[u] - gx0;          // shared column of byte 0
+                if (lo[u] == 0 && hi[u] == 16 && (reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
+                    u32 *dw = reinterpret_cast<u32 *>(drow + x);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        dw[2 * k] = __byte_perm(wv[k], 0u, 0x4140);
+                        dw[2 * k + 1] = __byte_perm(wv[k], 0u, 0x4342);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i >= lo[u] && i < hi[u]) drow[x + i] = (u16)((wv[i >> 2] >> (8 * (i & 3))) & 0xffu);
+                }
+            } else {
+                const int x = (int)(xblk[u] >> 1) - gx0;
+                if (lo[u] == 0 && hi[u] == 16 && (reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
+                    u32 *dw = reinterpret_cast<u32 *>(drow + x);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dw[k] = wv[k];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (2 * i >= lo[u] && 2 * i < hi[u])
+                            drow[x + i] = (u16)((wv[i >> 1] >> (16 * (i & 1))) & 0xffffu);
+                }
             }
         }
     }
-    __syncthreads();
-    // --- k = 5 .. Smax on the compacted worklist, one warp per pixel
-    unsigned int *cur = sm.wl0, *nxt = sm.wl1;
-    int ci = 0;
-    for (int k = 5; k <= smax; k += 2) {
-        const int n = s_cnt[ci];
-        if (n == 0) break;
-        if (threadIdx.x == 0) s_cnt[ci ^ 1] = 0;
+    // halo columns and zero rows
+    const bool left = gx0 < 0, right = gx0 + cols > W;
+    const bool zrows = zero_outside && (gy0 < 0 || gy0 + rows > H);
+    if (left || right || zrows) {
         __syncthreads();
-        for (int e = warp; e < n; e += kThreads / 32) {
-            const unsigned ent = cur[e];
-            const int ry = (int)(ent >> 16), rx = (int)(ent & 0xffffu);
-            const unsigned short *c = sm.gs + (ry + Ra) * GW + (rx + Ra);
-            const unsigned zxy = c[0];
-            const WinStats st = warp_window_stats(c, GW, k, lane);
+        for (int i = threadIdx.x; i < rows * cols; i += kThreads) {
+            const int r = i / cols, c = i - r * cols;
+            const int gx = gx0 + c, gy = gy0 + r;
+            const bool xout = (unsigned)gx >= (unsigned)W;
+            if (zero_outside && ((unsigned)gy >= (unsigned)H || xout)) {
+                dst[r * ds + c] = 0;
+            } else if (xout) {
+                const int sc = refl(gx, W) - gx0;
+                dst[r * ds + c] = (sc >= 0 && sc < cols) ? dst[r * ds + sc] : (u16)0;
+            }
+        }
+    }
+}
+
+// Store rows [0, th) x cols [0, tw) of a shared u16 region (row stride ss,
+// first element src, even column) to an image at (y0, x0), x0 even; one
+// warp per row, one pixel pair per lane (one 16- or 32-bit store when the
+// image address allows).
+__device__ void store_region(const u16 *src, int ss, int th, int tw, uint8_t *base, long long pitch, int es, int y0,
+                             int x0)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = 2 * lane;
+    if (c >= tw) return;
+    const bool two = c + 1 < tw;
+    for (int r = warp; r < th; r += kWarps) {
+        uint8_t *px = base + (long long)(y0 + r) * pitch + (long long)(x0 + c) * es;
+        const u32 pr = *reinterpret_cast<const u32 *>(src + r * ss + c);
+        if (es == 1) {
+            if (two && (reinterpret_cast<uintptr_t>(px) & 1) == 0) {
+                *reinterpret_cast<u16 *>(px) = (u16)__byte_perm(pr, 0u, 0x4420);
+            } else {
+                px[0] = (uint8_t)pr;
+                if (two) px[1] = (uint8_t)(pr >> 16);
+            }
+        } else {
+            if (two && (reinterpret_cast<uintptr_t>(px) & 3) == 0) {
+                *reinterpret_cast<u32 *>(px) = pr;
+            } else {
+                reinterpret_cast<u16 *>(px)[0] = (u16)pr;
+                if (two) reinterpret_cast<u16 *>(px)[1] = (u16)(pr >> 16);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- median, 3x3
+// Append the pixels flagged in this warp to a worklist (row << 6 | col).
+__device__ __forceinline__ void wl_append(bool flo, bool fhi, int r, int lane, u16 *wl, int *cnt)
+{
+    const u32 blo = __ballot_sync(FULL, flo), bhi = __ballot_sync(FULL, fhi);
+    if ((blo | bhi) == 0u) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(cnt, __popc(blo) + __popc(bhi));
+    base = __shfl_sync(FULL, base, 0);
+    const u32 lt = (1u << lane) - 1u;
+    if (flo) wl[base + __popc(blo & lt)] = (u16)((r << 6) | (2 * lane));
+    if (fhi) wl[base + __popc(blo) + __popc(bhi & lt)] = (u16)((r << 6) | (2 * lane + 1));
+}
+
+// 3x3 stage, packed: values < 2^15, two pixels per lane.
+__device__ void amf3_packed(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl, int *cnt, int FH)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RS = FH / kWarps;
+    const int r0 = warp * RS, r1 = min(r0 + RS, g.nrow);
+    if (r0 >= r1) return;
+    const bool on_lo = 2 * lane < g.ncol, on_hi = 2 * lane + 1 < g.ncol;
+    const bool smax3 = d.smax == 3, keep = d.unresolved != 0;
+    const u32 *gw = reinterpret_cast<const u32 *>(gs);
+    const int GSw = g.GS >> 1;
+    const int wb = ((g.Ra + g.pa) >> 1) + lane;
+    u32 *fw = reinterpret_cast<u32 *>(fs);
+
+    auto rowsort = [&](int fr, u32 &lo, u32 &mid, u32 &hi, u32 &ctr) {
+        const u32 *row = gw + (fr + g.Ra) * GSw + wb;
+        const u32 wm = row[-1], w0 = row[0], wp = row[1];
+        u32 a = __byte_perm(wm, w0, 0x5432), b = w0, c = __byte_perm(w0, wp, 0x5432);
+        ctr = b;
+        const u32 l1 = vmin(a, b), h1 = vmax(a, b);
+        lo = vmin(l1, c);
+        const u32 t = vmax(l1, c);
+        mid = vmin(h1, t);
+        hi = vmax(h1, t);
+    };
+    u32 pl, pm, ph, pc, cl, cm, ch, cc;
+    rowsort(r0 - 1, pl, pm, ph, pc);
+    rowsort(r0, cl, cm, ch, cc);
+#pragma unroll 4
+    for (int r = r0; r < r1; ++r) {
+        u32 nl, nm, nh, nc;
+        rowsort(r + 1, nl, nm, nh, nc);
+        const u32 zmin = vmin(vmin(pl, cl), nl), maxlo = vmax(vmax(pl, cl), nl);
+        const u32 zmax = vmax(vmax(ph, ch), nh), minhi = vmin(vmin(ph, ch), nh);
+        const u32 zmed = vmed3(maxlo, vmed3(pm, cm, nm), minhi);
+        const u32 zxy = cc;
+        // lane-wise zmin <= zmed, zxy <= zmax: the differences never borrow
+        const u32 pa_ = (vmin(zmed - zmin, zmax - zmed) + 0x7fff7fffu) & 0x80008000u;   // level A per lane
+        const u32 pb_ = (vmin(zxy - zmin, zmax - zxy) + 0x7fff7fffu) & 0x80008000u;    // level B per lane
+        const u32 kb = (pb_ >> 15) * 0xffffu;
+        u32 out = (zxy & kb) | (zmed & ~kb);
+        bool flo = false, fhi = false;
+        if (pa_ != 0x80008000u) {
+            const u32 fa = ((~pa_ & 0x80008000u) >> 15) * 0xffffu;    // lanes failing level A
+            const u32 alt = (smax3 && keep) ? zxy : zmed;
+            out = (out & ~fa) | (alt & fa);
+            if (!smax3) {
+                flo = on_lo && !(pa_ & 0x8000u);
+                fhi = on_hi && !(pa_ & 0x80000000u);
+            }
+        }
+        if (on_lo) fw[r * (FS / 2) + lane] = out;
+        if (!smax3) wl_append(flo, fhi, r, lane, wl, cnt);
+        pl = cl; pm = cm; ph = ch; pc = cc;
+        cl = nl; cm = nm; ch = nh; cc = nc;
+    }
+}
+
+// 3x3 stage, scalar (full 16-bit range): the same schedule, one pixel at a time.
+__device__ void amf3_scalar(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl, int *cnt, int FH)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RS = FH / kWarps;
+    const int r0 = warp * RS, r1 = min(r0 + RS, g.nrow);
+    if (r0 >= r1) return;
+    const bool smax3 = d.smax == 3, keep = d.unresolved != 0;
+    const int cbase = g.Ra + g.pa + 2 * lane;
+    for (int half = 0; half < 2; ++half) {
+        const int col = 2 * lane + half;
+        const bool on = col < g.ncol;
+        const int gc = cbase + half;
+        auto rowsort = [&](int fr, u32 &lo, u32 &mid, u32 &hi, u32 &ctr) {
+            const u16 *row = gs + (fr + g.Ra) * g.GS + gc;
+            u32 a = row[-1], b = row[0], c = row[1];
+            ctr = b;
+            const u32 l1 = umin(a, b), h1 = umax(a, b);
+            lo = umin(l1, c);
+            const u32 t = umax(l1, c);
+            mid = umin(h1, t);
+            hi = umax(h1, t);
+        };
+        u32 pl, pm, ph, pc, cl, cm, ch, cc;
+        rowsort(r0 - 1, pl, pm, ph, pc);
+        rowsort(r0, cl, cm, ch, cc);
+        for (int r = r0; r < r1; ++r) {
+            u32 nl, nm, nh, nc;
+            rowsort(r + 1, nl, nm, nh, nc);
+            const u32 zmin = umin(umin(pl, cl), nl), maxlo = umax(umax(pl, cl), nl);
+            const u32 zmax = umax(umax(ph, ch), nh), minhi = umin(umin(ph, ch), nh);
+            const u32 zmed = smed3(maxlo, smed3(pm, cm, nm), minhi);
+            const u32 zxy = cc;
+            u32 out;
+            bool grow = false;
+            if (zmin < zmed && zmed < zmax) out = (zmin < zxy && zxy < zmax) ? zxy : zmed;
+            else if (smax3) out = keep ? zxy : zmed;
+            else { out = zmed; grow = on; }
+            if (on) fs[r * FS + col] = (u16)out;
+            if (!smax3) wl_append(half == 0 && grow, half == 1 && grow, r, lane, wl, cnt);
+            pl = cl; pm = cm; ph = ch; pc = cc;
+            cl = nl; cm = nm; ch = nh; cc = nc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- median, window growth
+__device__ __forceinline__ void cex(u32 &a, u32 &b)
+{
+    const u32 t = umin(a, b);
+    b = umax(a, b);
+    a = t;
+}
+
+// Forgetful selection: min of a[0..S-1] to a[0], max to a[S-1].
+template <int S>
+__device__ __forceinline__ void minmax_ends(u32 *a)
+{
+#pragma unroll
+    for (int i = 0; i + 1 < S; i += 2) cex(a[i], a[i + 1]);
+#pragma unroll
+    for (int i = 2; i < S; i += 2) cex(a[0], a[i]);
+#pragma unroll
+    for (int i = 1; i < S - 1; i += 2) cex(a[i], a[S - 1]);
+}
+
+template <int S>
+__device__ __forceinline__ void forget_round(u32 *a, u32 v)
+{
+    minmax_ends<S>(a);
+    a[0] = v;     // drop the min (a[0]) and the max (a[S-1]), insert the next sample
+}
+
+// Median of the 5x5 window at ctr by forgetful selection: start with 14
+// samples; 11 times discard the min and max of the working set (neither can
+// be the median of the rest) and add the next sample; the median of the last
+// three is the window median.
+__device__ u32 median25(const u16 *ctr, int GS)
+{
+    u32 a[14];
+#pragma unroll
+    for (int i = 0; i < 14; ++i) a[i] = ctr[(i / 5 - 2) * GS + (i % 5 - 2)];
+#define HD_SAMPLE(i) ((u32)ctr[((i) / 5 - 2) * GS + ((i) % 5 - 2)])
+    forget_round<14>(a, HD_SAMPLE(14));
+    forget_round<13>(a, HD_SAMPLE(15));
+    forget_round<12>(a, HD_SAMPLE(16));
+    forget_round<11>(a, HD_SAMPLE(17));
+    forget_round<10>(a, HD_SAMPLE(18));
+    forget_round<9>(a, HD_SAMPLE(19));
+    forget_round<8>(a, HD_SAMPLE(20));
+    forget_round<7>(a, HD_SAMPLE(21));
+    forget_round<6>(a, HD_SAMPLE(22));
+    forget_round<5>(a, HD_SAMPLE(23));
+    forget_round<4>(a, HD_SAMPLE(24));
+#undef HD_SAMPLE
+    return smed3(a[0], a[1], a[2]);
+}
+
+// The (K*K-1)/2-th smallest sample of the K x K window at ctr, known to lie
+// strictly between zmin and zmax: the least t with #{v <= t} > (K*K-1)/2, by
+// bisection on t with one counting pass per step.
+template <int K>
+__device__ u32 median_bisect(const u16 *ctr, int GS, u32 zmin, u32 zmax)
+{
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    u32 lo = zmin + 1, hi = zmax - 1;
+    while (lo < hi) {
+        const u32 mid = (lo + hi) >> 1;
+        u32 c = 0;
+#pragma unroll 1
+        for (int dy = -R; dy <= R; ++dy) {
+            const u16 *row = ctr + dy * GS;
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) c += (u32)row[dx] <= mid;
+        }
+        if (c > (u32)M0) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// One window size for every pixel on the worklist `cur` (n entries):
+//   level A holds iff neither zmin nor zmax fills more than half the window
+//   (the median equals zmin exactly when #{v == zmin} > (K*K-1)/2, and zmax
+//   likewise);
+//   level B with zmin < zxy < zmax keeps zxy; otherwise the pixel needs the
+//   median and joins the selection list (stored from the top of `nxt`);
+//   pixels failing level A go to `nxt` for the next window, or at Smax take
+//   the median (zmin or zmax by the counts) or keep zxy.
+template <int K>
+__device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur, int n, u16 *nxt, int cap,
+                           int *cnt_next, int *cnt_sel, bool last, bool keep)
+{
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    for (int e0 = 0; e0 < n; e0 += kThreads) {
+        const int e = e0 + threadIdx.x;
+        bool to_next = false, to_sel = false;
+        u32 ent = 0;
+        if (e < n) {
+            ent = cur[e];
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
+            const u32 zxy = ctr[0];
+            u32 zmin = 0xffffu, zmax = 0u;
+#pragma unroll(K == 5 ? K : 1)
+            for (int dy = -R; dy <= R; ++dy) {
+                const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    const u32 v = row[dx];
+                    zmin = umin(zmin, v);
+                    zmax = umax(zmax, v);
+                }
+            }
+            u32 cmin = 0, cmax = 0;
+#pragma unroll(K == 5 ? K : 1)
+            for (int dy = -R; dy <= R; ++dy) {
+                const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    const u32 v = row[dx];
+                    cmin += v == zmin;
+                    cmax += v == zmax;
+                }
+            }
+            if (cmin <= (u32)M0 && cmax <= (u32)M0) {
+                if (zmin < zxy && zxy < zmax) fs[r * FS + c] = (u16)zxy;
+                else to_sel = true;
+            } else if (last) {
+                fs[r * FS + c] = (u16)(keep ? zxy : (cmin > (u32)M0 ? zmin : zmax));
+            } else {
+                to_next = true;
+            }
+        }
+        const u32 bn = __ballot_sync(FULL, to_next), bs_ = __ballot_sync(FULL, to_sel);
+        if (bn | bs_) {
+            int pn = 0, ps = 0;
             if (lane == 0) {
-                if (st.zmin < st.zmed && st.zmed < st.zmax) {
-                    sm.fs[ry * FW + rx] = (unsigned short)((st.zmin < zxy && zxy < st.zmax) ? zxy : st.zmed);
-                } else if (k == smax) {
-                    sm.fs[ry * FW + rx] = (unsigned short)(keep ? zxy : st.zmed);
-                } else {
-                    const int p = atomicAdd(&s_cnt[ci ^ 1], 1);
-                    nxt[p] = ent;
+                if (bn) pn = atomicAdd(cnt_next, __popc(bn));
+                if (bs_) ps = atomicAdd(cnt_sel, __popc(bs_));
+            }
+            pn = __shfl_sync(FULL, pn, 0);
+            ps = __shfl_sync(FULL, ps, 0);
+            const u32 lt = (1u << lane) - 1u;
+            if (to_next) nxt[pn + __popc(bn & lt)] = (u16)ent;
+            if (to_sel) nxt[cap - 1 - (ps + __popc(bs_ & lt))] = (u16)ent;
+        }
+    }
+}
+
+template <int K>
+__device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel)
+{
+    constexpr int R = K / 2;
+    for (int e = threadIdx.x; e < nsel; e += kThreads) {
+        const u32 ent = *(sel_top - e);
+        const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+        const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
+        u32 zmed;
+        if (K == 5) {
+            zmed = median25(ctr, g.GS);
+        } else {
+            u32 zmin = 0xffffu, zmax = 0u;
+#pragma unroll 1
+            for (int dy = -R; dy <= R; ++dy) {
+                const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    const u32 v = row[dx];
+                    zmin = umin(zmin, v);
+                    zmax = umax(zmax, v);
                 }
             }
+            zmed = median_bisect<K>(ctr, g.GS, zmin, zmax);
+        }
+        fs[r * FS + c] = (u16)zmed;
+    }
+}
+
+// Windows k = 5..Smax for the pixels that failed level A at k = 3.
+__device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl0, u16 *wl1, int *cnt,
+                         int cap)
+{
+    const bool keep = d.unresolved != 0;
+    u16 *cur = wl0, *nxt = wl1;
+    int ci = 0;
+    for (int k = 5; k <= d.smax; k += 2) {
+        const int n = cnt[ci];
+        if (n == 0) break;
+        if (threadIdx.x == 0) {
+            cnt[ci ^ 1] = 0;
+            cnt[2] = 0;
         }
         __syncthreads();
-        unsigned int *t = cur; cur = nxt; nxt = t;
+        const bool last = k == d.smax;
+        switch (k) {
+        case 5: grow_level<5>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        case 7: grow_level<7>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        case 9: grow_level<9>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        case 11: grow_level<11>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        case 13: grow_level<13>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        default: grow_level<15>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        }
+        __syncthreads();
+        const int nsel = cnt[2];
+        if (nsel > 0) {
+            const u16 *top = nxt + cap - 1;
+            switch (k) {
+            case 5: select_level<5>(g, gs, fs, top, nsel); break;
+            case 7: select_level<7>(g, gs, fs, top, nsel); break;
+            case 9: select_level<9>(g, gs, fs, top, nsel); break;
+            case 11: select_level<11>(g, gs, fs, top, nsel); break;
+            case 13: select_level<13>(g, gs, fs, top, nsel); break;
+            default: select_level<15>(g, gs, fs, top, nsel); break;
+            }
+            __syncthreads();
+        }
+        u16 *t = cur; cur = nxt; nxt = t;
         ci ^= 1;
     }
 }
 
-// Vertical sums over w rows for output rows [0, th) of the f region.
-__device__ void vertical_sums(const Smem &sm, int FW, int th, int w)
+// ---------------------------------------------------------------- Wiener sums
+// Horizontal box sums of f over the w-column window of every output column
+// x in [0, tw), for f rows [0, nrow):
+//   H1[j][x] = sum_{t<w} f[j][x + hx + t],  H2 = the same of f^2.
+// One thread slides along eight columns of one row; the lanes of a warp take
+// 32 consecutive rows (conflict-free shared reads).  NARROW: H2 as u32
+// (exact values; the S2 sums built from them may wrap), WIDE: H2 as u64.
+template <bool NARROW>
+__device__ void hsums(const Geo &g, const u16 *fs, u32 *H1, void *h2p, int w, bool with_h2)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int SEG = 4;
-    const int nseg = (th + SEG - 1) / SEG;
-    const int ncc = (FW + 31) >> 5;
-    for (int it = warp; it < nseg * ncc; it += kThreads / 32) {
-        const int seg = it / ncc, cc = it - seg * ncc;
-        const int c = cc * 32 + lane;
-        if (c >= FW) continue;
-        const int oy0 = seg * SEG, oy1 = min(th, oy0 + SEG);
-        unsigned s1 = 0;
-        unsigned long long s2 = 0;
-        for (int dy = 0; dy < w; ++dy) {
-            const unsigned v = sm.fs[(oy0 + dy) * FW + c];
-            s1 += v;
-            s2 += (unsigned long long)(v * v);
+    const int groups = (g.nrow + 31) >> 5, runs = (g.tw + 7) >> 3;
+    for (int job = warp; job < groups * runs; job += kWarps) {
+        const int grp = job / runs, m = job - grp * runs;
+        const int j = grp * 32 + lane;
+        if (j >= g.nrow) continue;
+        const int xs = 8 * m, xe = min(xs + 8, g.tw);
+        const u16 *fr = fs + j * FS + g.hx;
+        u32 *h1 = H1 + j * HS;
+        u32 s1 = 0;
+        u64 s2 = 0;
+        for (int t = 0; t < w; ++t) {
+            const u32 f = fr[xs + t];
+            s1 += f;
+            if (with_h2) s2 += (u64)(f * f);
         }
-        sm.V1[oy0 * FW + c] = s1;
-        sm.V2[oy0 * FW + c] = s2;
-        for (int oy = oy0 + 1; oy < oy1; ++oy) {
-            const unsigned vin = sm.fs[(oy + w - 1) * FW + c];
-            const unsigned vout = sm.fs[(oy - 1) * FW + c];
-            s1 += vin - vout;
-            s2 += (unsigned long long)(vin * vin);
-            s2 -= (unsigned long long)(vout * vout);
-            sm.V1[oy * FW + c] = s1;
-            sm.V2[oy * FW + c] = s2;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int x = xs + i;
+            if (x < xe) {
+                h1[x] = s1;
+                if (with_h2) {
+                    if (NARROW) reinterpret_cast<u32 *>(h2p)[j * HS + x] = (u32)s2;
+                    else reinterpret_cast<u64 *>(h2p)[j * HS + x] = s2;
+                }
+                if (x + 1 < xe) {
+                    const u32 a = fr[x + w], b = fr[x];
+                    s1 += a - b;
+                    if (with_h2) {
+                        s2 += (u64)(a * a);
+                        s2 -= (u64)(b * b);
+                    }
+                }
+            }
         }
     }
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
+// Number of (pixel, window offset) pairs whose sample lands on index y of an
+// axis of length N under the border rule (window radius r).
+__device__ u32 window_multiplicity(int y, int N, int r, bool zero)
+{
+    if (zero) return (u32)(min(r, y) + min(r, N - 1 - y) + 1);
+    if (y >= r && y <= N - 1 - r) return (u32)(2 * r + 1);
+    u32 m = 0;
+    const long long lo = -r, hi = (long long)N - 1 + r, P = 2LL * N;
+    for (int fam = 0; fam < 2; ++fam) {
+        const long long base = fam ? (-1LL - y) : (long long)y;     // refl(t) == y
+        long long k = (lo - base) >= 0 ? (lo - base + P - 1) / P : -((base - lo) / P);
+        for (long long t = base + k * P; t <= hi; t += P) {
+            if (t < lo) continue;
+            const long long a = max(-(long long)r, t - N + 1), b = min((long long)r, t);
+            if (b >= a) m += (u32)(b - a + 1);
+        }
+    }
+    return m;
+}
+
+// ---------------------------------------------------------------- exactness helpers
+__device__ __forceinline__ u64 warp_sum_u64(u64 x)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
     return x;
 }
 
+// Add v to the split sum (lo32 + hi32 * 2^32): two fire-and-forget reductions.
+__device__ __forceinline__ void split_add(u64 *lo32, u64 *hi32, u64 v)
+{
+    atomicAdd(lo32, v & 0xffffffffull);
+    atomicAdd(hi32, v >> 32);
+}
+
+// hi32 * 2^32 + lo32 as a 128-bit value {hi, lo}.
+__device__ __forceinline__ void split_total(u64 lo32, u64 hi32, u64 &hi, u64 &lo)
+{
+    lo = lo32 + (hi32 << 32);
+    hi = (hi32 >> 32) + (lo < lo32 ? 1ull : 0ull);
+}
+
 // Correctly rounded conversion of hi*2^64 + lo to binary64.
-__device__ double u128_to_double(unsigned long long hi, unsigned long long lo)
+__device__ double u128_to_double(u64 hi, u64 lo)
 {
     if (hi == 0) return __ull2double_rn(lo);
     const int s = __clzll((long long)hi);
-    unsigned long long top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
-    const unsigned long long rest = lo << s;
+    u64 top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
+    const u64 rest = lo << s;
     top |= (rest != 0ull) ? 1ull : 0ull;    // sticky bit, far below the rounding position
     return scalbn(__ull2double_rn(top), 64 - s);
 }
 
-__device__ bool wait_phase1(const ImgDesc &d, unsigned total, unsigned long long limit, int *s_flag)
+// nu2 = fl(fl(n * B - A) / (n^2 H W)) from the two exact per-image sums.
+__device__ double noise_variance(const ImgCtl *ctl, u64 n, int H, int W)
+{
+    u64 alo, ahi, blo, bhi;
+    split_total(__ldcg(&ctl->A_lo32), __ldcg(&ctl->A_hi32), ahi, alo);
+    split_total(__ldcg(&ctl->B_lo32), __ldcg(&ctl->B_hi32), bhi, blo);
+    const u64 nlo = blo * n;
+    const u64 nhi = __umul64hi(blo, n) + bhi * n;
+    const u64 dlo = nlo - alo;
+    const u64 dhi = nhi - ahi - (nlo < alo ? 1ull : 0ull);
+    const double denom = (double)n * (double)n * (double)H * (double)W;
+    return __ddiv_rn(u128_to_double(dhi, dlo), denom);
+}
+
+__device__ bool wait_phase1(const ImgDesc &d, u32 total, u64 limit, int *s_flag)
 {
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned long long polls = 0;
-        volatile unsigned int *cnt = &d.ctl->p1_done;
+        u64 polls = 0;
+        volatile u32 *cnt = &d.ctl->p1_done;
         while (*cnt < total) {
             if (++polls > limit) {
                 atomicOr(&g_device_error, DEVERR_TIMEOUT);
@@ -325,181 +793,401 @@ __device__ bool wait_phase1(const ImgDesc &d, unsigned total, unsigned long long
 }
 
 struct BlockShared {
-    int item[2];
-    int cnt[2];
+    int item[3];      // current / next ticket (double buffer), next ticket for the prefetch
+    const ImgCtl *nu2_of;   // image whose noise variance is cached below
+    double nu2;
+    float nu2f;
+    int cnt[3];
     int flag;
-    unsigned long long red[kThreads / 32];
+    u64 red[2][kWarps];
+    u32 my[128];
+    u32 mx[FW];
 };
 
-__device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Smem &sm,
-                         BlockShared &bs, int nextbuf, bool &prefetched)
+// ---------------------------------------------------------------- Wiener passes
+// Phase-1 statistics of one tile: sum over its pixels of S1^2 (A) and of
+// M(q) f_q^2 (B); added to the image's exact sums.
+template <bool NARROW>
+__device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, BlockShared &bs)
 {
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int tyi = tile / d.tiles_x, txi = tile - tyi * d.tiles_x;
-    const int x0 = txi * lp.tile_w, y0 = tyi * lp.tile_h;
-    const int tw = min(lp.tile_w, d.W - x0), th = min(lp.tile_h, d.H - y0);
-    const int mode = d.mode;
-    const bool two_phase = (mode == MODE_WIENER_EST || mode == MODE_HYBRID_EST);
-    const bool do_amf = phase == 1 && (mode == MODE_AMF || mode == MODE_HYBRID_EST || mode == MODE_HYBRID_GIVEN);
-    const int Rw = mode == MODE_AMF ? 0 : (d.w >> 1);
-    const int Ra = do_amf ? (d.smax >> 1) : 0;
-    const int FW = tw + 2 * Rw, FH = th + 2 * Rw;
-
-    if (phase == 2) {
-        const unsigned total = (unsigned)(d.tiles_x * d.tiles_y);
-        const bool ok = wait_phase1(d, total, lp.spin_limit, &bs.flag);
-        if (tid == 0 && lp.ticket) bs.item[nextbuf] = (int)atomicAdd(lp.ticket, 1u);
-        prefetched = true;
-        if (!ok) return;
-    }
-
-    // ---- fill the f region in shared memory
-    if (do_amf) {
-        const int GW = FW + 2 * Ra, GH = FH + 2 * Ra;
-        if (tid == 0) bs.cnt[0] = 0;
-        load_region(sm.gs, GW, GH, d.src, d.src_pitch, d.elem, d.H, d.W, y0 - Rw - Ra, x0 - Rw - Ra,
-                    false, false);
-        __syncthreads();
-        amf_region(d, sm, FW, FH, GW, Ra, bs.cnt);
-        __syncthreads();
-        if (Rw > 0 && d.border_zero) {
-            // zero-border Wiener: samples outside the image read 0
-            for (int i = tid; i < FW * FH; i += kThreads) {
-                const int ry = i / FW, rx = i - ry * FW;
-                const int gy = y0 - Rw + ry, gx = x0 - Rw + rx;
-                if ((unsigned)gy >= (unsigned)d.H || (unsigned)gx >= (unsigned)d.W) sm.fs[i] = 0;
-            }
-            __syncthreads();
-        }
-    } else {
-        const bool from_f = (phase == 2 && mode == MODE_HYBRID_EST);
-        load_region(sm.fs, FW, FH, from_f ? d.fbuf : d.src, from_f ? d.f_pitch : d.src_pitch, d.elem,
-                    d.H, d.W, y0 - Rw, x0 - Rw, d.border_zero != 0, from_f);
-        __syncthreads();
-    }
-
-    // ---- median only: store and finish
-    if (mode == MODE_AMF) {
-        for (int oy = warp; oy < th; oy += kThreads / 32) {
-            uint8_t *row = d.dst + (long long)(y0 + oy) * d.dst_pitch;
-            for (int ox = lane; ox < tw; ox += 32) {
-                const unsigned v = sm.fs[oy * FW + ox];
-                if (d.elem == 1) row[x0 + ox] = (uint8_t)v;
-                else reinterpret_cast<unsigned short *>(row)[x0 + ox] = (unsigned short)v;
-            }
-        }
-        return;
-    }
-
-    // ---- phase 1 of the hybrid keeps the median output for phase 2
-    if (phase == 1 && mode == MODE_HYBRID_EST) {
-        for (int oy = warp; oy < th; oy += kThreads / 32) {
-            uint8_t *row = d.fbuf + (long long)(y0 + oy) * d.f_pitch;
-            for (int ox = lane; ox < tw; ox += 32) {
-                const unsigned v = sm.fs[(oy + Rw) * FW + ox + Rw];
-                if (d.elem == 1) row[x0 + ox] = (uint8_t)v;
-                else reinterpret_cast<unsigned short *>(row)[x0 + ox] = (unsigned short)v;
-            }
-        }
-    }
-
-    // ---- local statistics
     const int w = d.w;
-    vertical_sums(sm, FW, th, w);
+    hsums<NARROW>(g, fs, H1, nullptr, w, false);
+    const bool zero = d.border_zero != 0;
+    const bool interior = !zero && g.y0 >= g.Rw && g.y0 + g.th <= d.H - g.Rw && g.x0 >= g.Rw &&
+                          g.x0 + g.tw <= d.W - g.Rw;
+    if (!interior) {
+        for (int i = threadIdx.x; i < g.th + g.tw; i += kThreads) {
+            if (i < g.th) bs.my[i] = window_multiplicity(g.y0 + i, d.H, g.Rw, zero);
+            else bs.mx[i - g.th] = window_multiplicity(g.x0 + i - g.th, d.W, g.Rw, zero);
+        }
+    }
     __syncthreads();
-    const unsigned long long n = (unsigned long long)w * (unsigned long long)w;
-
-    if (phase == 1 && two_phase) {
-        // sum of D over the tile, exact
-        unsigned long long acc = 0;
-        for (int oy = warp; oy < th; oy += kThreads / 32) {
-            for (int ox = lane; ox < tw; ox += 32) {
-                unsigned long long S1 = 0, S2 = 0;
-                for (int dx = 0; dx < w; ++dx) {
-                    S1 += sm.V1[oy * FW + ox + dx];
-                    S2 += sm.V2[oy * FW + ox + dx];
-                }
-                acc += n * S2 - S1 * S1;
-            }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = 2 * lane;
+    const int per = (g.th + kWarps - 1) / kWarps;
+    const int j0 = warp * per, j1 = min(j0 + per, g.th);
+    u64 accA = 0, accB = 0;
+    if (x < g.tw && j0 < j1) {
+        const bool two = x + 1 < g.tw;
+        u32 sa = 0, sb = 0;
+        for (int t = 0; t < w; ++t) {
+            const uint2 h = *reinterpret_cast<const uint2 *>(H1 + (j0 + t) * HS + x);
+            sa += h.x;
+            sb += h.y;
         }
-        acc = warp_sum_u64(acc);
-        if (lane == 0) bs.red[warp] = acc;
-        __threadfence();   // f tile and everything above visible before the done count
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long s = 0;
-            for (int i = 0; i < kThreads / 32; ++i) s += bs.red[i];
-            const unsigned long long old = atomicAdd(&d.ctl->sumD_lo, s);
-            if (old + s < old) atomicAdd(&d.ctl->sumD_hi, 1ull);
-            __threadfence();
-            atomicAdd(&d.ctl->p1_done, 1u);
-        }
-        return;
-    }
-
-    // ---- Wiener apply
-    double nu2 = d.noise_var;
-    if (two_phase) {
-        unsigned long long lo, hi;
-        lo = __ldcg(&d.ctl->sumD_lo);
-        hi = __ldcg(&d.ctl->sumD_hi);
-        const double denom = (double)n * (double)n * (double)d.H * (double)d.W;
-        nu2 = __ddiv_rn(u128_to_double(hi, lo), denom);
-    }
-    if (tile == 0 && tid == 0 && d.noise_var_out) *d.noise_var_out = nu2;
-    const float v2 = __double2float_rn(nu2);
-    const float inv_n = __frcp_rn((float)n);
-    const float inv_n2 = __frcp_rn((float)(n * n));
-    const float maxv = (float)d.maxv;
-    for (int oy = warp; oy < th; oy += kThreads / 32) {
-        uint8_t *row = d.dst + (long long)(y0 + oy) * d.dst_pitch;
-        for (int ox = lane; ox < tw; ox += 32) {
-            unsigned long long S1 = 0, S2 = 0;
-            for (int dx = 0; dx < w; ++dx) {
-                S1 += sm.V1[oy * FW + ox + dx];
-                S2 += sm.V2[oy * FW + ox + dx];
-            }
-            const unsigned long long D = n * S2 - S1 * S1;
-            const unsigned fv = sm.fs[(oy + Rw) * FW + ox + Rw];
-            const float mu = __fmul_rn(__ull2float_rn(S1), inv_n);
-            const float s2 = __fmul_rn(__ull2float_rn(D), inv_n2);
-            const float den = fmaxf(s2, v2);
-            const float num = fmaxf(__fsub_rn(s2, v2), 0.0f);
-            float y;
-            if (den > 0.0f) {
-                const float gain = __fdiv_rn(num, den);
-                const float dev = __fsub_rn(__uint2float_rn(fv), mu);
-                y = __fadd_rn(mu, __fmul_rn(gain, dev));
+        for (int j = j0; j < j1; ++j) {
+            const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
+            const u32 fa = fp & 0xffffu, fb = fp >> 16;
+            if (interior) {
+                accA += (u64)sa * sa + (two ? (u64)sb * sb : 0ull);
+                accB += (u64)(fa * fa) + (two ? (u64)(fb * fb) : 0ull);
             } else {
-                y = mu;
+                const u32 my = bs.my[j];
+                accA += (u64)sa * sa;
+                accB += (u64)(fa * fa) * (my * bs.mx[x]);
+                if (two) {
+                    accA += (u64)sb * sb;
+                    accB += (u64)(fb * fb) * (my * bs.mx[x + 1]);
+                }
             }
-            float q = floorf(__fadd_rn(y, 0.5f));
-            q = fminf(fmaxf(q, 0.0f), maxv);
-            const unsigned out = (unsigned)q;
-            if (d.elem == 1) row[x0 + ox] = (uint8_t)out;
-            else reinterpret_cast<unsigned short *>(row)[x0 + ox] = (unsigned short)out;
-            if (d.y_out) d.y_out[(long long)(y0 + oy) * d.W + x0 + ox] = y;
+            if (j + 1 < j1) {
+                const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
+                const uint2 ho_ = *reinterpret_cast<const uint2 *>(H1 + j * HS + x);
+                sa += hi_.x - ho_.x;
+                sb += hi_.y - ho_.y;
+            }
+        }
+    }
+    if (interior) accB *= (u64)w * (u64)w;
+    accA = warp_sum_u64(accA);
+    accB = warp_sum_u64(accB);
+    if (lane == 0) {
+        bs.red[0][warp] = accA;
+        bs.red[1][warp] = accB;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 sa = 0, sb = 0;
+        for (int i = 0; i < kWarps; ++i) {
+            sa += bs.red[0][i];
+            sb += bs.red[1][i];
+        }
+        split_add(&d.ctl->A_lo32, &d.ctl->A_hi32, sa);
+        split_add(&d.ctl->B_lo32, &d.ctl->B_hi32, sb);
+        // release: the CTA's f tile (ordered before this thread by the barrier)
+        // and the sums become visible before the done count
+        __threadfence();
+        atomicAdd(&d.ctl->p1_done, 1u);
+    }
+}
+
+struct ApplyConst {
+    u32 n;
+    float v2f, inv_n, inv_n2, maxv;
+};
+
+// binary32 Wiener output of one pixel (fixed evaluation order, see top).
+__device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyConst &k, float &y)
+{
+    const float mu = __fmul_rn(__uint2float_rn(s1), k.inv_n);
+    const float s2 = __fmul_rn(dfl, k.inv_n2);
+    const float den = fmaxf(s2, k.v2f);
+    const float num = fmaxf(__fsub_rn(s2, k.v2f), 0.0f);
+    if (den > 0.0f) {
+        const float gain = __fdiv_rn(num, den);
+        y = __fadd_rn(mu, __fmul_rn(gain, __fsub_rn(__uint2float_rn(fv), mu)));
+    } else {
+        y = mu;
+    }
+    float q = floorf(__fadd_rn(y, 0.5f));
+    q = fminf(fmaxf(q, 0.0f), k.maxv);
+    return (u32)q;
+}
+
+// Wiener apply of one tile: vertical sliding sums of H1, H2 per column pair,
+// two output pixels per lane and row, stored as one pixel pair.
+template <bool NARROW>
+__device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, void *h2p, float v2f)
+{
+    const int w = d.w;
+    hsums<NARROW>(g, fs, H1, h2p, w, true);
+    __syncthreads();
+    ApplyConst k;
+    k.n = (u32)(w * w);
+    k.v2f = v2f;
+    k.inv_n = __frcp_rn((float)k.n);
+    k.inv_n2 = __frcp_rn((float)(k.n * k.n));
+    k.maxv = (float)d.maxv;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = 2 * lane;
+    const int per = (g.th + kWarps - 1) / kWarps;
+    const int j0 = warp * per, j1 = min(j0 + per, g.th);
+    if (x >= g.tw || j0 >= j1) return;
+    const bool two = x + 1 < g.tw;
+    const u32 *H2n = reinterpret_cast<const u32 *>(h2p);
+    const u64 *H2w = reinterpret_cast<const u64 *>(h2p);
+    u32 sa = 0, sb = 0;
+    u32 qa = 0, qb = 0;       // NARROW: S2 mod 2^32
+    u64 wa = 0, wb = 0;       // WIDE
+    for (int t = 0; t < w; ++t) {
+        const uint2 h = *reinterpret_cast<const uint2 *>(H1 + (j0 + t) * HS + x);
+        sa += h.x;
+        sb += h.y;
+        if (NARROW) {
+            const uint2 q = *reinterpret_cast<const uint2 *>(H2n + (j0 + t) * HS + x);
+            qa += q.x;
+            qb += q.y;
+        } else {
+            wa += H2w[(j0 + t) * HS + x];
+            wb += H2w[(j0 + t) * HS + x + 1];
+        }
+    }
+    for (int j = j0; j < j1; ++j) {
+        float da, db;
+        if (NARROW) {
+            da = __uint2float_rn(k.n * qa - sa * sa);     // exact: the true value is < 2^32
+            db = __uint2float_rn(k.n * qb - sb * sb);
+        } else {
+            da = __ull2float_rn((u64)k.n * wa - (u64)sa * sa);
+            db = __ull2float_rn((u64)k.n * wb - (u64)sb * sb);
+        }
+        const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
+        float ya, yb;
+        const u32 oa = wiener_px(sa, da, fp & 0xffffu, k, ya);
+        const u32 ob = wiener_px(sb, db, fp >> 16, k, yb);
+        uint8_t *px = d.dst + (long long)(g.y0 + j) * d.dst_pitch + (long long)(g.x0 + x) * d.elem;
+        if (d.elem == 1) {
+            if (two && (reinterpret_cast<uintptr_t>(px) & 1) == 0) {
+                *reinterpret_cast<u16 *>(px) = (u16)(oa | (ob << 8));
+            } else {
+                px[0] = (uint8_t)oa;
+                if (two) px[1] = (uint8_t)ob;
+            }
+        } else {
+            if (two && (reinterpret_cast<uintptr_t>(px) & 3) == 0) {
+                *reinterpret_cast<u32 *>(px) = oa | (ob << 16);
+            } else {
+                reinterpret_cast<u16 *>(px)[0] = (u16)oa;
+                if (two) reinterpret_cast<u16 *>(px)[1] = (u16)ob;
+            }
+        }
+        if (d.y_out) {
+            float *yp = d.y_out + (long long)(g.y0 + j) * d.W + g.x0 + x;
+            yp[0] = ya;
+            if (two) yp[1] = yb;
+        }
+        if (j + 1 < j1) {
+            const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
+            const uint2 ho_ = *reinterpret_cast<const uint2 *>(H1 + j * HS + x);
+            sa += hi_.x - ho_.x;
+            sb += hi_.y - ho_.y;
+            if (NARROW) {
+                const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + w) * HS + x);
+                const uint2 qo = *reinterpret_cast<const uint2 *>(H2n + j * HS + x);
+                qa += qi.x - qo.x;
+                qb += qi.y - qo.y;
+            } else {
+                wa += H2w[(j + w) * HS + x];
+                wa -= H2w[j * HS + x];
+                wb += H2w[(j + w) * HS + x + 1];
+                wb -= H2w[j * HS + x + 1];
+            }
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) hd_persistent_kernel(const __grid_constant__ LaunchParams lp)
+// ---------------------------------------------------------------- one work item
+struct Views {
+    u16 *fs, *gs, *wl0, *wl1;
+    u32 *h1;
+    void *h2;
+};
+
+__device__ __forceinline__ int find_segment(const Seg *segs, int nsegs, int item)
+{
+    int lo = 0, hi = nsegs - 1;
+    while (lo < hi) {   // last segment with first <= item
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool mode_median(int mode)
+{
+    return mode == MODE_AMF || mode == MODE_HYBRID_EST || mode == MODE_HYBRID_GIVEN;
+}
+
+// Tile geometry of an image with Wiener halo rw (0 for the median alone).
+__device__ __forceinline__ void tile_shape(int rw, int FH, int &Lm, int &TW, int &TH)
+{
+    Lm = rw + (rw & 1);
+    TW = (FW - Lm - rw) & ~1;
+    TH = FH - 2 * rw;
+}
+
+// Warp 0 asks L2 for the noisy-input rows of the next median tile, so its
+// region load finds them on chip.  Only bytes inside image rows are touched.
+__device__ void prefetch_item(const LaunchParams &lp, int item)
+{
+    if (threadIdx.x >= 32 || item >= lp.total_items) return;
+    const Seg *segs = lp.segs ? lp.segs : lp.oneseg;
+    const Seg sg = segs[find_segment(segs, lp.nsegs, item)];
+    if (sg.phase != 1) return;
+    const ImgDesc &d = lp.descs ? lp.descs[sg.img] : lp.one;
+    if (!mode_median(d.mode)) return;
+    const int tile = item - sg.first;
+    const int Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1), Ra = d.smax >> 1;
+    int Lm, TW, TH;
+    tile_shape(Rw, lp.region_h, Lm, TW, TH);
+    const int tyi = tile / d.tiles_x, txi = tile - tyi * d.tiles_x;
+    const int x0 = txi * TW, y0 = tyi * TH;
+    const int tw = min(TW, d.W - x0), th = min(TH, d.H - y0);
+    const int gx0 = x0 - Lm - Ra - 1, gy0 = y0 - Rw - Ra;
+    const int rows = th + 2 * (Rw + Ra), cols = tw + Lm + Rw + 2 * Ra + 2;
+    const int xa = max(gx0, 0), xb = min(gx0 + cols, d.W);
+    for (int r = threadIdx.x; r < rows; r += 32) {
+        const uint8_t *rp = d.src + (long long)refl(gy0 + r, d.H) * d.src_pitch;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(rp + (long long)xa * d.elem);
+        const uintptr_t b = reinterpret_cast<uintptr_t>(rp + (long long)xb * d.elem);
+        for (uintptr_t line = a & ~uintptr_t(127); line < b; line += 128) {
+            const uintptr_t p = line < a ? a : line;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
+    }
+}
+
+template <bool PACK, bool NARROW>
+__device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const LaunchParams &lp, const Views &vw,
+                           BlockShared &bs, const int &next)
+{
+    const int mode = d.mode;
+    const int FH = lp.region_h;
+    const bool do_amf = phase == 1 && mode_median(mode);
+    HD_STAMP_INIT();
+
+    // ---- the f region in shared memory
+    if (do_amf) {
+        if (threadIdx.x == 0) bs.cnt[0] = 0;
+        load_region(vw.gs + g.pa, g.GS, g.nrow + 2 * g.Ra, g.ncol + 2 * g.Ra, d.src, d.src_pitch, d.elem, d.H, d.W,
+                    g.gfy - g.Ra, g.gfx - g.Ra, false, false);
+        // the next ticket (taken when this item started) has arrived by now
+        if (lp.ticket && threadIdx.x == 0) bs.item[2] = next;
+        __syncthreads();
+        HD_STAMP(0);
+        if (lp.ticket) prefetch_item(lp, bs.item[2]);
+        if (PACK) amf3_packed(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
+        else amf3_scalar(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
+        __syncthreads();
+        HD_STAMP(1);
+        if (d.smax > 3) amf_grow(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW);
+        if (g.Rw > 0 && d.border_zero) {
+            // zero-border Wiener: samples outside the image read 0
+            for (int i = threadIdx.x; i < g.nrow * g.ncol; i += kThreads) {
+                const int r = i / g.ncol, c = i - r * g.ncol;
+                const int gy = g.gfy + r, gx = g.gfx + c;
+                if ((unsigned)gy >= (unsigned)d.H || (unsigned)gx >= (unsigned)d.W) vw.fs[r * FS + c] = 0;
+            }
+        }
+        __syncthreads();
+    } else {
+        const bool from_f = (phase == 2 && mode == MODE_HYBRID_EST);
+        load_region(vw.fs, FS, g.nrow, g.ncol, from_f ? d.fbuf : d.src, from_f ? d.f_pitch : d.src_pitch, d.elem,
+                    d.H, d.W, g.gfy, g.gfx, d.border_zero != 0, from_f);
+        __syncthreads();
+        HD_STAMP(5);
+    }
+    if (do_amf) HD_STAMP(2);
+
+    if (mode == MODE_AMF) {
+        store_region(vw.fs, FS, g.th, g.tw, d.dst, d.dst_pitch, d.elem, g.y0, g.x0);
+        return;
+    }
+    if (phase == 1 && mode == MODE_HYBRID_EST) {
+        store_region(vw.fs + g.Rw * FS + g.Lm, FS, g.th, g.tw, d.fbuf, d.f_pitch, d.elem, g.y0, g.x0);
+        HD_STAMP(3);
+    }
+    if (phase == 1 && (mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST)) {
+        tile_stats<NARROW>(d, g, vw.fs, vw.h1, bs);
+        HD_STAMP(4);
+        return;
+    }
+    // one thread converts the noise variance (binary64 is slow here); the
+    // value is cached per CTA for the image's following tiles
+    if (threadIdx.x == 0) {
+        const bool est = mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST;
+        if (!est || bs.nu2_of != d.ctl) {
+            const u64 n = (u64)d.w * (u64)d.w;
+            const double nu2 = est ? noise_variance(d.ctl, n, d.H, d.W) : d.noise_var;
+            bs.nu2 = nu2;
+            bs.nu2f = __double2float_rn(nu2);
+            bs.nu2_of = est ? d.ctl : nullptr;
+        }
+        if (g.x0 == 0 && g.y0 == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
+    }
+    __syncthreads();
+    tile_apply<NARROW>(d, g, vw.fs, vw.h1, vw.h2, bs.nu2f);
+    HD_STAMP(6);
+}
+
+__device__ __forceinline__ bool image_narrow(const ImgDesc &d)
+{
+    const long long n = (long long)d.w * d.w;
+    return d.maxv < 0x8000 && (long long)(d.w + 1) * d.maxv <= 65535 && n * d.maxv < 131072;
+}
+
+__device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Views &vw,
+                         BlockShared &bs, const int &next)
+{
+    Geo g;
+    g.Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1);
+    int TW, TH;
+    tile_shape(g.Rw, lp.region_h, g.Lm, TW, TH);
+    g.hx = g.Lm - g.Rw;
+    g.Ra = (phase == 1 && mode_median(d.mode)) ? (d.smax >> 1) : 0;
+    g.pa = g.Ra & 1;
+    g.GS = g_stride(g.Ra);
+    const int tyi = tile / d.tiles_x, txi = tile - tyi * d.tiles_x;
+    g.x0 = txi * TW;
+    g.y0 = tyi * TH;
+    g.tw = min(TW, d.W - g.x0);
+    g.th = min(TH, d.H - g.y0);
+    g.ncol = g.Lm + g.tw + g.Rw;
+    g.nrow = g.th + 2 * g.Rw;
+    g.gfx = g.x0 - g.Lm;
+    g.gfy = g.y0 - g.Rw;
+
+    if (phase == 2) {
+        HD_STAMP_INIT();
+        const bool ok = wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag);
+        HD_STAMP(7);
+        if (!ok) return;
+    }
+    const bool pack = d.maxv < 0x8000;
+    const bool narrow = image_narrow(d);
+    if (pack && narrow) run_item_t<true, true>(d, phase, g, lp, vw, bs, next);
+    else if (pack) run_item_t<true, false>(d, phase, g, lp, vw, bs, next);
+    else run_item_t<false, false>(d, phase, g, lp, vw, bs, next);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid_constant__ LaunchParams lp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockShared bs;
-    const SmemLayout L = layout(lp.tile_w, lp.tile_h, lp.ra_max, lp.rw_max);
-    Smem sm;
-    sm.V2 = reinterpret_cast<unsigned long long *>(smem_raw + L.v2);
-    sm.V1 = reinterpret_cast<unsigned int *>(smem_raw + L.v1);
-    sm.wl0 = reinterpret_cast<unsigned int *>(smem_raw + L.wl0);
-    sm.wl1 = reinterpret_cast<unsigned int *>(smem_raw + L.wl1);
-    sm.gs = reinterpret_cast<unsigned short *>(smem_raw + L.gs);
-    sm.fs = reinterpret_cast<unsigned short *>(smem_raw + L.fs);
+    const SmemLayout L = layout(lp.region_h, lp.ra_max, lp.wide);
+    Views vw;
+    vw.fs = reinterpret_cast<u16 *>(smem_raw + L.fs);
+    vw.gs = reinterpret_cast<u16 *>(smem_raw + L.gs);
+    vw.wl0 = reinterpret_cast<u16 *>(smem_raw + L.wl);
+    vw.wl1 = vw.wl0 + lp.region_h * FW;
+    vw.h1 = reinterpret_cast<u32 *>(smem_raw + L.h1);
+    vw.h2 = smem_raw + L.h2;
 
     const Seg *segs = lp.segs ? lp.segs : lp.oneseg;
     int buf = 0;
     int item;
+    if (threadIdx.x == 0) bs.nu2_of = nullptr;
     if (lp.ticket) {
         if (threadIdx.x == 0) bs.item[0] = (int)atomicAdd(lp.ticket, 1u);
         __syncthreads();
@@ -508,20 +1196,16 @@ __global__ void __launch_bounds__(kThreads) hd_persistent_kernel(const __grid_co
         item = blockIdx.x;
     }
     while (item < lp.total_items) {
-        int lo = 0, hi = lp.nsegs - 1;
-        while (lo < hi) {           // last segment with first <= item
-            const int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].first <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const Seg sg = segs[lo];
+        const Seg sg = segs[find_segment(segs, lp.nsegs, item)];
         const ImgDesc &d = lp.descs ? lp.descs[sg.img] : lp.one;
-        bool prefetched = false;
-        if (lp.ticket && sg.phase == 1) {
-            if (threadIdx.x == 0) bs.item[buf ^ 1] = (int)atomicAdd(lp.ticket, 1u);
-            prefetched = true;
-        }
-        run_item(d, sg.phase, item - sg.first, lp, sm, bs, buf ^ 1, prefetched);
+        // Take the next ticket now and read it after the item: its latency
+        // hides behind the work.  Tickets only grow, and an item waits only on
+        // earlier tickets, so the CTA holding the earliest unfinished ticket
+        // is always working on it: holding a later one cannot deadlock.
+        int next = 0;
+        if (lp.ticket && threadIdx.x == 0) next = (int)atomicAdd(lp.ticket, 1u);
+        run_item(d, sg.phase, item - sg.first, lp, vw, bs, next);
+        if (lp.ticket && threadIdx.x == 0) bs.item[buf ^ 1] = next;
         __syncthreads();
         if (lp.ticket) {
             buf ^= 1;
@@ -534,13 +1218,16 @@ __global__ void __launch_bounds__(kThreads) hd_persistent_kernel(const __grid_co
     // for the next launch on this workspace.
     if (lp.ticket && threadIdx.x == 0) {
         __threadfence();
-        const unsigned done = atomicAdd(lp.ticket + 1, 1u);
+        const u32 done = atomicAdd(lp.ticket + 1, 1u);
         if (done == gridDim.x - 1) {
             __threadfence();
             for (int i = 0; i < lp.nctl; ++i) {
-                lp.ctl_reset[i].sumD_lo = 0;
-                lp.ctl_reset[i].sumD_hi = 0;
-                lp.ctl_reset[i].p1_done = 0;
+                ImgCtl &c = lp.ctl_reset[i];
+                c.A_lo32 = 0;
+                c.A_hi32 = 0;
+                c.B_lo32 = 0;
+                c.B_hi32 = 0;
+                c.p1_done = 0;
             }
             lp.ticket[0] = 0;
             lp.ticket[1] = 0;
@@ -551,9 +1238,9 @@ __global__ void __launch_bounds__(kThreads) hd_persistent_kernel(const __grid_co
 
 }  // namespace
 
-size_t smem_bytes(int tile_w, int tile_h, int ra_max, int rw_max)
+size_t smem_bytes(int region_h, int ra_max, int wide)
 {
-    return layout(tile_w, tile_h, ra_max, rw_max).total;
+    return layout(region_h, ra_max, wide).total;
 }
 
 int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *stream)
@@ -571,6 +1258,12 @@ int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *strea
 
 int max_ctas_per_sm(size_t smem)
 {
+    // occupancy per shared-memory size, cached (the query is not free)
+    static size_t keys[16];
+    static int vals[16];
+    static int used = 0;
+    for (int i = 0; i < used; ++i)
+        if (keys[i] == smem) return vals[i];
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(hd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -579,6 +1272,11 @@ int max_ctas_per_sm(size_t smem)
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_persistent_kernel, kThreads, smem) != cudaSuccess)
         return 0;
+    if (used < 16) {
+        keys[used] = smem;
+        vals[used] = n;
+        ++used;
+    }
     return n;
 }
 
@@ -589,6 +1287,18 @@ int sm_count()
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     return n;
 }
+
+#ifdef HD_STAGE_PROFILE
+extern "C" int hd_debug_stage_cycles(unsigned long long *out16, int clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(out16, g_stage_cycles, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess && clear) {
+        unsigned long long z[16] = {0};
+        e = cudaMemcpyToSymbol(g_stage_cycles, z, sizeof(z));
+    }
+    return (int)e;
+}
+#endif
 
 int read_and_clear_device_error(unsigned int *out)
 {

@@ -110,14 +110,11 @@ def test_workspace_sizes():
 def test_tuning_validation():
     old = hd.hd_get_tuning()
     try:
-        with pytest.raises(hd.HDError):
-            hd.hd_set_tuning(7, 32)
-        with pytest.raises(hd.HDError):
-            hd.hd_set_tuning(64, 2)
-        with pytest.raises(hd.HDError):
-            hd.hd_set_tuning(64, 32, 9)
-        hd.hd_set_tuning(32, 16, 2)
-        assert hd.hd_get_tuning() == (32, 16, 2)
+        for bad in ((8, 0), (20, 0), (136, 0), (32, 9), (32, -1)):
+            with pytest.raises(hd.HDError):
+                hd.hd_set_tuning(*bad)
+        hd.hd_set_tuning(64, 2)
+        assert hd.hd_get_tuning() == (64, 2)
     finally:
         hd.hd_set_tuning(*old)
 

@@ -134,13 +134,13 @@ def test_amf_full_range_16bit_and_constant():
     np.testing.assert_array_equal(gpu_amf(c, 11), c)
 
 
-@pytest.mark.parametrize("tile", [(8, 4), (32, 16), (64, 32), (128, 64), (256, 8), (40, 12)])
+@pytest.mark.parametrize("tile", [(16, 0), (24, 1), (32, 0), (64, 3), (128, 0)])
 def test_amf_independent_of_tiling(tile):
     g = noisy_image(150, 211, np.uint16, seed=9)
     ref = oracle.amf(g, 11)
     old = hd.hd_get_tuning()
     try:
-        hd.hd_set_tuning(*tile, 0)
+        hd.hd_set_tuning(*tile)
         np.testing.assert_array_equal(gpu_amf(g, 11), ref)
         f, nu2, _ = gpu_hybrid(g, 11, 5, bits=12)
         _, r = oracle.hybrid(g, 11, 5, bits=12)
