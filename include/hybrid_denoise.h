@@ -140,6 +140,27 @@ hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_by
 hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p,
                                      size_t *bytes);
 
+/* The hybrid with no device allocation anywhere: the scratch (median plane
+ * and queue counters) is one array of HD_STATIC_SCRATCH_BYTES in device
+ * memory that the library declares, so a caller that cannot call cudaMalloc
+ * (a fixed-budget real-time loop, a plug-in whose host owns the allocator)
+ * can still run the hybrid on its own src/dst buffers.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *   - Limit: images whose hybrid_workspace_size() exceeds
+ *     HD_STATIC_SCRATCH_BYTES (36 MiB: e.g. 4096 x 4096 at 16 bits fits, and
+ *     1620 x 1620 at 8 bits) are rejected with HD_ERR_OVERFLOW.
+ *   - Every GPU that loads the library holds the array until the process
+ *     exits.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls on a device share the one array: calls that overlap in time
+ *     on the GPU race and corrupt each other's results.  The array keeps the
+ *     last call's contents; each call clears the queue counters it needs.
+ * Same filtering, parameters, errors and output as hybrid_denoise. */
+#define HD_STATIC_SCRATCH_BYTES (36u * 1024u * 1024u)
+hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
+
 /* ---------------------------------------------------------------- batches
  * Many images of uneven sizes and per-image parameters in ONE persistent
  * kernel launch: a device work queue of (image, phase, tile) items where an

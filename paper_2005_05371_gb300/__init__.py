@@ -32,7 +32,7 @@ HD_WIENER_W_MAX = 15
 # every symbol include/hybrid_denoise.h declares
 EXPORTS = [
     "amf_filter", "wiener_filter", "wiener_workspace_size", "hybrid_denoise", "hybrid_workspace_size",
-    "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_batched",
+    "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_static", "hybrid_denoise_batched",
     "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
     "hd_status_str", "hd_version",
@@ -76,6 +76,7 @@ def _load() -> ctypes.CDLL:
         "hybrid_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hybrid_denoise_host": ([img_p, P, S, P], I),
         "hybrid_host_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
+        "hybrid_denoise_static": ([img_p, P], I),
         "hybrid_denoise_batched": ([img_p, I, P, S, P], I),
         "hybrid_batched_workspace_size": ([img_p, I, ctypes.POINTER(S)], I),
         "hd_batch_plan_create": ([img_p, I, P, S, ctypes.POINTER(P)], I),
@@ -270,6 +271,17 @@ def hybrid_denoise_host(src: np.ndarray, dst: np.ndarray, smax: int = 11, wiener
         workspace = _workspace(hybrid_host_workspace_size(H, W, code, p), "cuda")
     _check(_lib.hybrid_denoise_host(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace),
                                     _stream_ptr(stream)), "hybrid_denoise_host")
+    return dst
+
+
+def hybrid_denoise_static(src, dst, smax: int = 11, wiener_w: int = 5, noise_var: float = -1.0,
+                          border: int = HD_BORDER_SYMMETRIC, unresolved: int = HD_UNRESOLVED_ZMED,
+                          bits: int | None = None, noise_var_out=None, y_out=None, stream=None):
+    """Hybrid denoise without any device allocation: scratch is a fixed array
+    inside the library (for callers that cannot allocate device memory)."""
+    p = Params(smax, wiener_w, noise_var, border, unresolved, bits)
+    img = make_image(src, dst, p, noise_var_out, y_out)
+    _check(_lib.hybrid_denoise_static(ctypes.byref(img), _stream_ptr(stream)), "hybrid_denoise_static")
     return dst
 
 

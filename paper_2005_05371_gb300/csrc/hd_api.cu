@@ -313,6 +313,18 @@ std::vector<uint8_t> table_image(const BatchLayout &L, const BatchTables &bt)
 
 }  // namespace
 
+namespace hd {
+int hybrid_on_workspace(const void *img_, void *ws, size_t ws_bytes, void *stream)
+{
+    const hd_image *img = static_cast<const hd_image *>(img_);
+    hd_status st = check_image(img, true, true, false);
+    if (st != HD_OK) return st;
+    return run_single(img, hybrid_mode(img), ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t hybrid_control_bytes() { return ctl_bytes(); }
+}  // namespace hd
+
 struct hd_batch_plan {
     void *ws = nullptr;
     LaunchParams lp;

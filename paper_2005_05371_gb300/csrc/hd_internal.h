@@ -100,6 +100,13 @@ int sm_count();
 // Device error word helpers.
 int read_and_clear_device_error(unsigned int *out);
 
+// hybrid_denoise on a caller-provided workspace (used by the entry point whose
+// scratch is a static device array); returns an hd_status value.
+int hybrid_on_workspace(const void *img, void *ws, size_t ws_bytes, void *stream);
+
+// Bytes at the start of a hybrid workspace that must be zero before a launch.
+size_t hybrid_control_bytes();
+
 constexpr int kThreads = 256;
 constexpr unsigned int DEVERR_TIMEOUT = 1u;
 
