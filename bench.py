@@ -62,9 +62,10 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the persistent kernel's sources (the counters in profiles/ refer to it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_05371_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in ("hd_kernel.cu", "hd_internal.h"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -136,6 +137,35 @@ class ClockSampler:
         busy = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- multi-rank helpers
+def replica_seeds(name: str, rank: int):
+    """(phantom, noise) seeds of rank `rank`'s replica: every rank denoises its
+    own independent images (weak scaling, no data-path collective)."""
+    import synth
+    if name in synth.CONFIGS:
+        s = synth.CONFIGS[name]
+        return [(s.phantom_seed + 1000 * rank, s.noise_seed + 1000 * rank)]
+    if name == "batched":
+        return [(sp.phantom_seed, sp.noise_seed) for sp in synth.batch_specs(256, master_seed=400 + rank)]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time (all_reduce MAX); the identity for one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(px_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job Mpixel/s: pixels of all ranks over the slowest rank's time."""
+    return world * px_per_rank * steps / (max_ms / 1e3) / 1e6
 
 
 # --------------------------------------------------------------------------- workloads
@@ -396,13 +426,9 @@ def main():
     if status != hd.HD_OK:
         raise SystemExit(f"device error after the timed region: {hd.hd_status_str(status)}")
 
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = world * px_per_step * args.steps / (total_ms / 1e3) / 1e6
+    value = weak_value(px_per_step, args.steps, total_ms, world)
 
     # dominant (and only) kernel: one persistent launch per step; events over
     # back-to-back launches (graph replay) give the average launch duration

@@ -191,12 +191,14 @@ _BATCH_SIZES = [(256, 256), (512, 512), (768, 512), (1024, 1024)]
 def batch_specs(n: int = 256, master_seed: int = 400) -> list[SliceSpec]:
     """Uneven 12-bit slices: sizes from {256^2, 512^2, 768x512, 1024^2},
     sigma ~ U[10,60] LSB, density ~ U[0.01,0.5], Smax in {5,7,9,11},
-    Wiener window in {3,5,7}.  Slice i uses seeds derived from 400000+i."""
+    Wiener window in {3,5,7}.  Slice i uses phantom seed 1000*master+i and
+    noise seed 1000*master+100000+i (400000+i and 500000+i for master 400)."""
     rng = np.random.default_rng(master_seed)
     out = []
     for i in range(n):
         H, W = _BATCH_SIZES[int(rng.integers(0, len(_BATCH_SIZES)))]
         out.append(SliceSpec(H, W, "u16", 12, float(rng.uniform(10, 60)),
                              float(rng.uniform(0.01, 0.5)), int(rng.choice([5, 7, 9, 11])),
-                             int(rng.choice([3, 5, 7])), 400000 + i, 500000 + i, kind="ct"))
+                             int(rng.choice([3, 5, 7])), 1000 * master_seed + i, 1000 * master_seed + 100000 + i,
+                             kind="ct"))
     return out
