@@ -168,8 +168,9 @@ hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
  * so one image's Wiener overlaps another's median.  Each result is
  * bit-identical to the same image through hybrid_denoise (integer
  * reductions make the order irrelevant).
- * hybrid_denoise_batched copies the n descriptors into the workspace on
- * `stream` (not capturable in a CUDA graph; use a plan for that). */
+ * hybrid_denoise_batched writes the n descriptors into the workspace with
+ * small kernels on `stream` (their bytes travel as kernel parameters), so the
+ * call never waits for the device; the host array may be freed on return. */
 hd_status hybrid_denoise_batched(const hd_image *imgs, int n, void *workspace,
                                  size_t ws_bytes, hd_stream_t stream);
 hd_status hybrid_batched_workspace_size(const hd_image *imgs, int n, size_t *bytes);

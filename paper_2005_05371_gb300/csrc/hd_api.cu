@@ -436,15 +436,14 @@ hd_status hybrid_denoise_batched(const hd_image *imgs, int n, void *workspace, s
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<uint8_t> h = table_image(L, bt);
     uint8_t *base = static_cast<uint8_t *>(workspace);
-    if (cudaMemcpyAsync(base + L.desc_off, h.data(), h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return HD_ERR_CUDA;
-    if (cudaMemsetAsync(base, 0, L.desc_off, s) != cudaSuccess) return HD_ERR_CUDA;
     LaunchParams lp = batch_params(workspace, L, bt);
     int grid = 0;
     size_t smem = 0;
     st = finish_params(lp, current_tuning(), &grid, &smem);
     if (st != HD_OK) return st;
-    // a copy from pageable memory has consumed `h` when cudaMemcpyAsync returns
+    // the tables travel in kernel parameters: nothing here waits for the stream
+    if (launch_table_upload(base + L.desc_off, h.data(), h.size(), (void *)s) != 0) return HD_ERR_CUDA;
+    if (cudaMemsetAsync(base, 0, L.desc_off, s) != cudaSuccess) return HD_ERR_CUDA;
     if (launch_persistent(lp, grid, smem, (void *)s) != 0) return HD_ERR_CUDA;
     return HD_OK;
 }

@@ -90,6 +90,11 @@ struct LaunchParams {
 // Shared-memory bytes the kernel needs.
 size_t smem_bytes(int region_h, int ra_max, int wide);
 
+// Upload `bytes` of a host table to device memory with parameter-carrying
+// kernel launches on `stream` (asynchronous, capturable); returns cudaError_t.
+constexpr int kTableChunkBytes = 30 * 1024;
+int launch_table_upload(void *dst, const void *src, size_t bytes, void *stream);
+
 // Launch the persistent kernel; returns cudaError_t as int.
 int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *stream);
 

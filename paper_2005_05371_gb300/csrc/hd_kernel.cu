@@ -57,6 +57,7 @@
 // slow on this part).
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstring>
 #include "hd_internal.h"
 
 namespace hd {
@@ -1236,7 +1237,37 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
     }
 }
 
+// Copies a chunk of a host-built table, carried in the kernel parameters, to
+// device memory: table uploads need no host-side copy and no stream sync.
+struct TableChunk {
+    unsigned char *dst;
+    unsigned int n;
+    unsigned char bytes[kTableChunkBytes];
+};
+
+__global__ void hd_table_writer(const __grid_constant__ TableChunk c)
+{
+    for (unsigned int i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.bytes[i];
+}
+
 }  // namespace
+
+int launch_table_upload(void *dst, const void *src, size_t bytes, void *stream)
+{
+    static_assert(sizeof(TableChunk) <= 32000, "kernel parameter limit");
+    const unsigned char *s = static_cast<const unsigned char *>(src);
+    for (size_t off = 0; off < bytes; off += kTableChunkBytes) {
+        const size_t n = bytes - off < (size_t)kTableChunkBytes ? bytes - off : (size_t)kTableChunkBytes;
+        TableChunk c;
+        c.dst = static_cast<unsigned char *>(dst) + off;
+        c.n = (unsigned int)n;
+        memcpy(c.bytes, s + off, n);
+        hd_table_writer<<<1, 256, 0, (cudaStream_t)stream>>>(c);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return (int)e;
+    }
+    return 0;
+}
 
 size_t smem_bytes(int region_h, int ra_max, int wide)
 {
