@@ -394,6 +394,14 @@ def main():
 
     items = build_workload(args.workload, rank)
     cfg = describe(args.workload, items)
+    # work-item shape from the autotuner's table (paper_2005_05371_gb300/tuning.json)
+    from paper_2005_05371_gb300 import autotune
+    if args.workload == "batched":
+        tuning = autotune.choose(4096, 4096)      # many items: the large-image entry
+    else:
+        tuning = autotune.choose(items[0][0].H, items[0][0].W)
+    hd.hd_set_tuning(*tuning)
+    cfg["tuning"] = {"region_h": tuning[0], "ctas_per_sm": tuning[1]}
     stream = torch.cuda.current_stream(dev)
 
     def to_dev(a):
