@@ -115,7 +115,11 @@ hd_status amf_filter(const hd_image *img, hd_stream_t stream);
  *   dst = min(2^bits - 1, floor(y + 0.5)).
  * The sums are exact integers, nu2 is binary64, the gain and y are binary32
  * with a fixed evaluation order (documented with the kernel).
- * workspace: device, >= wiener_workspace_size() bytes, 256-byte aligned. */
+ * workspace: device, >= wiener_workspace_size() bytes, 256-byte aligned
+ * (the size includes a plane of 8 bytes per pixel for the binary32 mu and
+ * sigma2; a workspace without that room, down to the size returned for the
+ * same image with the plane left out, is accepted and recomputes the window
+ * sums in the second pass instead: same output, slower). */
 hd_status wiener_filter(const hd_image *img, void *workspace, size_t ws_bytes,
                         hd_stream_t stream);
 hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
@@ -125,10 +129,17 @@ hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, siz
  * median output stays in the workspace (L2-resident for images up to tens of
  * MB); with a caller-supplied noise_var >= 0 the whole hybrid is one pass and
  * needs no workspace.  Exactly one kernel is enqueued per call.
- * workspace: device, >= hybrid_workspace_size() bytes, 256-byte aligned. */
+ * workspace: device, 256-byte aligned, >= hybrid_min_workspace_size() bytes.
+ *   hybrid_workspace_size() (the median plane, the queue counters and a plane
+ *   of 8 bytes per pixel holding the binary32 local mean and variance) gives
+ *   the fastest path: the Wiener pass then streams those statistics instead
+ *   of recomputing the window sums.  hybrid_min_workspace_size() (no
+ *   statistics plane) is the least accepted; any size in between runs the
+ *   recompute path.  The output is bit-identical either way. */
 hd_status hybrid_denoise(const hd_image *img, void *workspace, size_t ws_bytes,
                          hd_stream_t stream);
 hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
+hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
 /* The hybrid over host buffers: img->src and img->dst are HOST pointers
  * (pinned memory gives overlap-free full-speed copies; pageable works).  The
@@ -146,9 +157,10 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
  * (a fixed-budget real-time loop, a plug-in whose host owns the allocator)
  * can still run the hybrid on its own src/dst buffers.  The paper has no
  * counterpart; this is a deployment convenience.
- *   - Limit: images whose hybrid_workspace_size() exceeds
+ *   - Limit: images whose hybrid_min_workspace_size() exceeds
  *     HD_STATIC_SCRATCH_BYTES (36 MiB: e.g. 4096 x 4096 at 16 bits fits, and
- *     1620 x 1620 at 8 bits) are rejected with HD_ERR_OVERFLOW.
+ *     1620 x 1620 at 8 bits) are rejected with HD_ERR_OVERFLOW.  Images whose
+ *     hybrid_workspace_size() also fits take the statistics-plane path.
  *   - Every GPU that loads the library holds the array until the process
  *     exits.
  *   - The first call on each device looks up the array's device address

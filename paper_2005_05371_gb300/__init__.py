@@ -32,7 +32,7 @@ HD_WIENER_W_MAX = 15
 # every symbol include/hybrid_denoise.h declares
 EXPORTS = [
     "amf_filter", "wiener_filter", "wiener_workspace_size", "hybrid_denoise", "hybrid_workspace_size",
-    "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_static", "hybrid_denoise_batched",
+    "hybrid_min_workspace_size", "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_static", "hybrid_denoise_batched",
     "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
     "hd_status_str", "hd_version",
@@ -74,6 +74,7 @@ def _load() -> ctypes.CDLL:
         "wiener_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hybrid_denoise": ([img_p, P, S, P], I),
         "hybrid_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
+        "hybrid_min_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hybrid_denoise_host": ([img_p, P, S, P], I),
         "hybrid_host_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hybrid_denoise_static": ([img_p, P], I),
@@ -207,6 +208,14 @@ def hybrid_workspace_size(H: int, W: int, dtype_code: int, params: Params) -> in
     n = ctypes.c_size_t()
     _check(_lib.hybrid_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)), ctypes.byref(n)),
            "hybrid_workspace_size")
+    return n.value
+
+
+def hybrid_min_workspace_size(H: int, W: int, dtype_code: int, params: Params) -> int:
+    """Least workspace hybrid_denoise accepts (no statistics plane: slower path)."""
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_min_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)),
+                                          ctypes.byref(n)), "hybrid_min_workspace_size")
     return n.value
 
 

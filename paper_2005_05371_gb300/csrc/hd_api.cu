@@ -91,8 +91,12 @@ int device_sms()
 
 size_t f_pitch_of(int W, int dtype) { return round_up((size_t)W * elem_size(dtype), 16); }
 
-// Workspace layout of a single image: [ticket][ImgCtl] [fbuf]
+// Workspace layout of a single image: [ticket][ImgCtl] [fbuf] [plane].  The
+// plane (binary32 mu, s2 per pixel) is optional: without it phase 2
+// recomputes the window sums from the f region.
 size_t ctl_bytes() { return round_up(kTicketBytes + sizeof(ImgCtl), kAlign); }
+
+size_t plane_bytes(int H, int W) { return round_up((size_t)H * (size_t)W * 2 * sizeof(float), kAlign); }
 
 size_t single_ws_bytes(int H, int W, int dtype, bool needs_fbuf)
 {
@@ -101,13 +105,20 @@ size_t single_ws_bytes(int H, int W, int dtype, bool needs_fbuf)
     return b;
 }
 
-ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl, uint8_t *fbuf)
+size_t single_ws_full(int H, int W, int dtype, bool needs_fbuf)
+{
+    return single_ws_bytes(H, W, dtype, needs_fbuf) + plane_bytes(H, W);
+}
+
+ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl, uint8_t *fbuf,
+                  float *plane = nullptr)
 {
     ImgDesc d;
     std::memset(&d, 0, sizeof(d));
     d.src = static_cast<const uint8_t *>(img->src);
     d.dst = static_cast<uint8_t *>(img->dst);
     d.fbuf = fbuf;
+    d.plane = plane;
     d.src_pitch = (long long)img->src_pitch;
     d.dst_pitch = (long long)img->dst_pitch;
     d.f_pitch = (long long)f_pitch_of(img->W, img->dtype);
@@ -170,18 +181,22 @@ hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, c
     ImgCtl *ctl = nullptr;
     unsigned int *ticket = nullptr;
     uint8_t *fbuf = nullptr;
+    float *plane = nullptr;
     if (two_phase) {
         if (!ws || ((uintptr_t)ws % kAlign)) return HD_ERR_WORKSPACE;
-        if (ws_bytes < single_ws_bytes(img->H, img->W, img->dtype, needs_fbuf)) return HD_ERR_WORKSPACE;
+        const size_t need = single_ws_bytes(img->H, img->W, img->dtype, needs_fbuf);
+        if (ws_bytes < need) return HD_ERR_WORKSPACE;
         ticket = static_cast<unsigned int *>(ws);
         ctl = reinterpret_cast<ImgCtl *>(static_cast<uint8_t *>(ws) + kTicketBytes);
         if (needs_fbuf) fbuf = static_cast<uint8_t *>(ws) + ctl_bytes();
+        if (ws_bytes >= need + plane_bytes(img->H, img->W))
+            plane = reinterpret_cast<float *>(static_cast<uint8_t *>(ws) + need);
     }
     LaunchParams lp;
     std::memset(&lp, 0, sizeof(lp));
     lp.descs = nullptr;
     lp.segs = nullptr;
-    lp.one = make_desc(img, mode, t, ctl, fbuf);
+    lp.one = make_desc(img, mode, t, ctl, fbuf, plane);
     const int tiles = lp.one.tiles_x * lp.one.tiles_y;
     lp.oneseg[0] = Seg{0, 1, 0, tiles};
     lp.nsegs = 1;
@@ -209,7 +224,8 @@ int hybrid_mode(const hd_image *img) { return img->p.noise_var < 0.0 ? MODE_HYBR
 // ---------------------------------------------------------------- batches
 struct BatchLayout {
     size_t ctl_off, desc_off, seg_off, fbuf_off, total;
-    std::vector<size_t> fbuf_offsets;   // per image, or SIZE_MAX when not needed
+    std::vector<size_t> fbuf_offsets;    // per image, or SIZE_MAX when not needed
+    std::vector<size_t> plane_offsets;   // per image, or SIZE_MAX when not needed
 };
 
 BatchLayout batch_layout(const hd_image *imgs, int n)
@@ -224,12 +240,16 @@ BatchLayout batch_layout(const hd_image *imgs, int n)
     off = round_up(off + sizeof(Seg) * (size_t)(2 * n), kAlign);
     L.fbuf_off = off;
     L.fbuf_offsets.resize(n);
+    L.plane_offsets.resize(n);
     for (int i = 0; i < n; ++i) {
         if (hybrid_mode(&imgs[i]) == MODE_HYBRID_EST) {
             L.fbuf_offsets[i] = off;
             off += round_up((size_t)imgs[i].H * f_pitch_of(imgs[i].W, imgs[i].dtype), kAlign);
+            L.plane_offsets[i] = off;
+            off += plane_bytes(imgs[i].H, imgs[i].W);
         } else {
             L.fbuf_offsets[i] = SIZE_MAX;
+            L.plane_offsets[i] = SIZE_MAX;
         }
     }
     L.total = off;
@@ -262,7 +282,8 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
     bt.descs.resize(n);
     for (int i = 0; i < n; ++i) {
         uint8_t *fb = L.fbuf_offsets[i] == SIZE_MAX ? nullptr : base + L.fbuf_offsets[i];
-        bt.descs[i] = make_desc(&imgs[i], hybrid_mode(&imgs[i]), t, ctl + i, fb);
+        float *pl = L.plane_offsets[i] == SIZE_MAX ? nullptr : reinterpret_cast<float *>(base + L.plane_offsets[i]);
+        bt.descs[i] = make_desc(&imgs[i], hybrid_mode(&imgs[i]), t, ctl + i, fb, pl);
         bt.ra_max = std::max(bt.ra_max, halo_a(bt.descs[i]));
         bt.wide |= image_wide(bt.descs[i]) ? 1 : 0;
     }
@@ -323,6 +344,12 @@ int hybrid_on_workspace(const void *img_, void *ws, size_t ws_bytes, void *strea
 }
 
 size_t hybrid_control_bytes() { return ctl_bytes(); }
+
+size_t hybrid_min_bytes(const void *img_)
+{
+    const hd_image *img = static_cast<const hd_image *>(img_);
+    return img->p.noise_var < 0.0 ? single_ws_bytes(img->H, img->W, img->dtype, true) : 0;
+}
 }  // namespace hd
 
 struct hd_batch_plan {
@@ -347,7 +374,7 @@ hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, siz
 {
     if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
     if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;
-    *bytes = p->noise_var < 0.0 ? single_ws_bytes(H, W, dtype, false) : 0;
+    *bytes = p->noise_var < 0.0 ? single_ws_full(H, W, dtype, false) : 0;
     return HD_OK;
 }
 
@@ -360,6 +387,14 @@ hd_status wiener_filter(const hd_image *img, void *workspace, size_t ws_bytes, h
 }
 
 hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes)
+{
+    if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
+    if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;
+    *bytes = p->noise_var < 0.0 ? single_ws_full(H, W, dtype, true) : 0;
+    return HD_OK;
+}
+
+hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes)
 {
     if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
     if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;

@@ -58,6 +58,9 @@ struct ImgDesc {
     int mode;
     int tiles_x, tiles_y;
     int pad;
+    float *plane;             // optional (estimated noise variance): per output pixel the
+                              // binary32 pair (mu, s2) left by phase 1, row-major, W pairs a row;
+                              // nullptr: phase 2 recomputes the sums from the f region
 };
 
 // A run of consecutive tickets belonging to one (image, phase).
@@ -111,6 +114,8 @@ int hybrid_on_workspace(const void *img, void *ws, size_t ws_bytes, void *stream
 
 // Bytes at the start of a hybrid workspace that must be zero before a launch.
 size_t hybrid_control_bytes();
+// Smallest workspace that hybrid_on_workspace accepts for the image (no plane).
+size_t hybrid_min_bytes(const void *img);
 
 constexpr int kThreads = 256;
 constexpr unsigned int DEVERR_TIMEOUT = 1u;

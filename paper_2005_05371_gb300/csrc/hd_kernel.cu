@@ -99,7 +99,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline int g_stride(int ra) { return FW + 2 * ra + 4; }
 
 struct SmemLayout {
-    size_t fs, gs, wl, h1, h2, total;
+    size_t fs, gs, wl, st, h1, h2, total;
 };
 
 // fs is live for the whole item; the median view (gs, worklists) and the
@@ -114,6 +114,10 @@ __host__ __device__ inline SmemLayout layout(int FH, int ra_max, int wide)
     a = align16(a + (size_t)(FH + 2 * ra_max) * g_stride(ra_max) * sizeof(u16));
     L.wl = a;
     a = align16(a + 2 * (size_t)FH * FW * sizeof(u16));
+    // growth state per region pixel (windows of 7 and more): zmin | zmax << 16,
+    // then the two counts as bytes
+    L.st = a;
+    if (ra_max >= 3) a = align16(a + (size_t)FH * FW * (sizeof(u32) + sizeof(u16)));
     size_t b = scratch;
     L.h1 = b;
     b = align16(b + (size_t)FH * HS * sizeof(u32));
@@ -151,15 +155,17 @@ __device__ __forceinline__ u32 vmed3(u32 a, u32 b, u32 c) { return vmax(vmin(a, 
 __device__ __forceinline__ u32 smed3(u32 a, u32 b, u32 c) { return umax(umin(a, b), umin(umax(a, b), c)); }
 
 // ---------------------------------------------------------------- region loads / stores
-template <typename T>
-__device__ __forceinline__ T ldg_any(const T *p, bool cg)
+template <bool CG, typename T>
+__device__ __forceinline__ T ldg_any(const T *p)
 {
-    return cg ? __ldcg(p) : __ldg(p);
+    if (CG) return __ldcg(p);
+    return __ldg(p);
 }
 
 // Bytes [lo, hi) of the aligned 16-byte block at blk, by aligned pieces, into
 // q0 (bytes 0..7) and q1 (bytes 8..15); nothing outside [lo, hi) is read.
-__device__ __forceinline__ void load_partial(const uint8_t *blk, int lo, int hi, bool cg, u64 &q0, u64 &q1)
+template <bool CG>
+__device__ __noinline__ void load_partial(const uint8_t *blk, int lo, int hi, u64 &q0, u64 &q1)
 {
     q0 = 0;
     q1 = 0;
@@ -167,16 +173,16 @@ __device__ __forceinline__ void load_partial(const uint8_t *blk, int lo, int hi,
         u64 v;
         int s;
         if ((lo & 7) == 0 && lo + 8 <= hi) {
-            v = ldg_any(reinterpret_cast<const unsigned long long *>(blk + lo), cg);
+            v = ldg_any<CG>(reinterpret_cast<const unsigned long long *>(blk + lo));
             s = 8;
         } else if ((lo & 3) == 0 && lo + 4 <= hi) {
-            v = ldg_any(reinterpret_cast<const unsigned int *>(blk + lo), cg);
+            v = ldg_any<CG>(reinterpret_cast<const unsigned int *>(blk + lo));
             s = 4;
         } else if ((lo & 1) == 0 && lo + 2 <= hi) {
-            v = ldg_any(reinterpret_cast<const unsigned short *>(blk + lo), cg);
+            v = ldg_any<CG>(reinterpret_cast<const unsigned short *>(blk + lo));
             s = 2;
         } else {
-            v = ldg_any(blk + lo, cg);
+            v = ldg_any<CG>(blk + lo);
             s = 1;
         }
         if (lo < 8) q0 |= v << (8 * lo);
@@ -189,12 +195,15 @@ __device__ __forceinline__ void load_partial(const uint8_t *blk, int lo, int hi,
 // at dst) with the image region whose top-left pixel is (gy0, gx0), gx0 even.
 // Rows are read from refl(gy) (or are zero outside, zero_outside); columns
 // outside the image are reflected from the loaded columns of the same row (or
-// zero).  Global reads use 16-byte vectors where a whole aligned block lies
-// inside the row, aligned narrower pieces at the two ends, and never touch a
-// byte outside the image rows.  Whole blocks whose first pixel lands on a
-// 4-byte aligned shared address go to shared memory as 32-bit pixel pairs.
+// zero).  Global reads are whole aligned 16-byte blocks covering each row's
+// bytes; a block may take bytes of a neighbouring row or of the row padding
+// (they are not stored) but never leaves the buffer [buf_lo, buf_hi): only
+// at the buffer's two ends are aligned narrower pieces used.  Whole blocks
+// whose first pixel lands on a 4-byte aligned shared address go to shared
+// memory as 32-bit pixel pairs.
+template <bool CG>
 __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t *base, long long pitch, int es,
-                            int H, int W, int gy0, int gx0, bool zero_outside, bool cg)
+                            int H, int W, int gy0, int gx0, bool zero_outside, const uint8_t *buf_hi)
 {
     const int xa = max(gx0, 0), xb = min(gx0 + cols, W);   // in-image columns, xa < xb
     const int J = ((xb - xa) * es + 15) / 16 + 1;          // blocks that can hold a row's bytes
@@ -223,16 +232,14 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
                 const uint8_t *blk = reinterpret_cast<const uint8_t *>(
                     (reinterpret_cast<uintptr_t>(a) & ~uintptr_t(15)) + 16 * (uintptr_t)bi);
                 if (blk >= b) continue;
-                const int l = blk < a ? (int)(a - blk) : 0;
-                const int h = blk + 16 > b ? (int)(b - blk) : 16;
-                lo[u] = l;
-                hi[u] = h;
+                lo[u] = blk < a ? (int)(a - blk) : 0;
+                hi[u] = blk + 16 > b ? (int)(b - blk) : 16;
                 xblk[u] = (long long)(blk - rp);    // byte offset of the block within the row
-                if (l == 0 && h == 16) {
-                    v[u] = ldg_any(reinterpret_cast<const uint4 *>(blk), cg);
+                if (blk >= base && blk + 16 <= buf_hi) {
+                    v[u] = ldg_any<CG>(reinterpret_cast<const uint4 *>(blk));
                 } else {
                     u64 q0, q1;
-                    load_partial(blk, l, h, cg, q0, q1);
+                    load_partial<CG>(blk, lo[u], hi[u], q0, q1);
                     v[u] = make_uint4((u32)q0, (u32)(q0 >> 32), (u32)q1, (u32)(q1 >> 32));
                 }
             }
@@ -244,12 +251,24 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
             const u32 wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
             if (es == 1) {
                 const int x = (int)xblk[u] - gx0;          // shared column of byte 0
-                if (lo[u] == 0 && hi[u] == 16 && (reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
+                if ((reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
                     u32 *dw = reinterpret_cast<u32 *>(drow + x);
+                    if (lo[u] == 0 && hi[u] == 16) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        dw[2 * k] = __byte_perm(wv[k], 0u, 0x4140);
-                        dw[2 * k + 1] = __byte_perm(wv[k], 0u, 0x4342);
+                        for (int k = 0; k < 4; ++k) {
+                            dw[2 * k] = __byte_perm(wv[k], 0u, 0x4140);
+                            dw[2 * k + 1] = __byte_perm(wv[k], 0u, 0x4342);
+                        }
+                    } else {
+                        // pairs wholly inside [lo, hi) as 32-bit stores, the ends singly
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int i0 = 2 * k;
+                            const u32 pr = __byte_perm(wv[k >> 1], 0u, (k & 1) ? 0x4342 : 0x4140);
+                            if (i0 >= lo[u] && i0 + 1 < hi[u]) dw[k] = pr;
+                            else if (i0 >= lo[u] && i0 < hi[u]) drow[x + i0] = (u16)(pr & 0xffffu);
+                            else if (i0 + 1 >= lo[u] && i0 + 1 < hi[u]) drow[x + i0 + 1] = (u16)(pr >> 16);
+                        }
                     }
                 } else {
 #pragma unroll
@@ -258,10 +277,15 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
                 }
             } else {
                 const int x = (int)(xblk[u] >> 1) - gx0;
-                if (lo[u] == 0 && hi[u] == 16 && (reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
+                if ((reinterpret_cast<uintptr_t>(drow + x) & 3) == 0) {
                     u32 *dw = reinterpret_cast<u32 *>(drow + x);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) dw[k] = wv[k];
+                    for (int k = 0; k < 4; ++k) {
+                        const int i0 = 4 * k;          // byte offset of the pair
+                        if (i0 >= lo[u] && i0 + 4 <= hi[u]) dw[k] = wv[k];
+                        else if (i0 >= lo[u] && i0 + 2 <= hi[u]) drow[x + 2 * k] = (u16)(wv[k] & 0xffffu);
+                        else if (i0 + 2 >= lo[u] && i0 + 4 <= hi[u]) drow[x + 2 * k + 1] = (u16)(wv[k] >> 16);
+                    }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
@@ -492,29 +516,6 @@ __device__ u32 median25(const u16 *ctr, int GS)
     return smed3(a[0], a[1], a[2]);
 }
 
-// The (K*K-1)/2-th smallest sample of the K x K window at ctr, known to lie
-// strictly between zmin and zmax: the least t with #{v <= t} > (K*K-1)/2, by
-// bisection on t with one counting pass per step.
-template <int K>
-__device__ u32 median_bisect(const u16 *ctr, int GS, u32 zmin, u32 zmax)
-{
-    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
-    u32 lo = zmin + 1, hi = zmax - 1;
-    while (lo < hi) {
-        const u32 mid = (lo + hi) >> 1;
-        u32 c = 0;
-#pragma unroll 1
-        for (int dy = -R; dy <= R; ++dy) {
-            const u16 *row = ctr + dy * GS;
-#pragma unroll
-            for (int dx = -R; dx <= R; ++dx) c += (u32)row[dx] <= mid;
-        }
-        if (c > (u32)M0) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
-}
-
 // One window size for every pixel on the worklist `cur` (n entries):
 //   level A holds iff neither zmin nor zmax fills more than half the window
 //   (the median equals zmin exactly when #{v == zmin} > (K*K-1)/2, and zmax
@@ -523,9 +524,13 @@ __device__ u32 median_bisect(const u16 *ctr, int GS, u32 zmin, u32 zmax)
 //   median and joins the selection list (stored from the top of `nxt`);
 //   pixels failing level A go to `nxt` for the next window, or at Smax take
 //   the median (zmin or zmax by the counts) or keep zxy.
+// The 5 x 5 window is scanned whole; from 7 x 7 on, only the new ring of
+// 4(K-1) samples is read and the extremes and their counts of the previous
+// window (kept per pixel in `st_mm` / `st_c`) are updated: a ring holding a
+// smaller minimum restarts its count, an equal one adds to it.
 template <int K>
 __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur, int n, u16 *nxt, int cap,
-                           int *cnt_next, int *cnt_sel, bool last, bool keep)
+                           int *cnt_next, int *cnt_sel, bool last, bool keep, u32 *st_mm, u16 *st_c)
 {
     constexpr int R = K / 2, M0 = (K * K - 1) / 2;
     const int lane = threadIdx.x & 31;
@@ -538,35 +543,76 @@ __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur,
             const int r = (int)(ent >> 6), c = (int)(ent & 63u);
             const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
             const u32 zxy = ctr[0];
-            u32 zmin = 0xffffu, zmax = 0u;
-#pragma unroll(K == 5 ? K : 1)
-            for (int dy = -R; dy <= R; ++dy) {
-                const u16 *row = ctr + dy * g.GS;
+            u32 zmin = 0xffffu, zmax = 0u, cmin = 0, cmax = 0;
+            if (K == 5) {
 #pragma unroll
-                for (int dx = -R; dx <= R; ++dx) {
-                    const u32 v = row[dx];
-                    zmin = umin(zmin, v);
-                    zmax = umax(zmax, v);
+                for (int dy = -R; dy <= R; ++dy) {
+                    const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                    for (int dx = -R; dx <= R; ++dx) {
+                        const u32 v = row[dx];
+                        zmin = umin(zmin, v);
+                        zmax = umax(zmax, v);
+                    }
                 }
-            }
-            u32 cmin = 0, cmax = 0;
-#pragma unroll(K == 5 ? K : 1)
-            for (int dy = -R; dy <= R; ++dy) {
-                const u16 *row = ctr + dy * g.GS;
 #pragma unroll
+                for (int dy = -R; dy <= R; ++dy) {
+                    const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                    for (int dx = -R; dx <= R; ++dx) {
+                        const u32 v = row[dx];
+                        cmin += v == zmin;
+                        cmax += v == zmax;
+                    }
+                }
+            } else {
+                const u16 *top = ctr - R * g.GS, *bot = ctr + R * g.GS;
+                u32 rmin = 0xffffu, rmax = 0u;
+#pragma unroll 4
                 for (int dx = -R; dx <= R; ++dx) {
-                    const u32 v = row[dx];
-                    cmin += v == zmin;
-                    cmax += v == zmax;
+                    const u32 a = top[dx], b = bot[dx];
+                    rmin = umin(rmin, umin(a, b));
+                    rmax = umax(rmax, umax(a, b));
+                }
+#pragma unroll 4
+                for (int dy = 1 - R; dy < R; ++dy) {
+                    const u32 a = ctr[dy * g.GS - R], b = ctr[dy * g.GS + R];
+                    rmin = umin(rmin, umin(a, b));
+                    rmax = umax(rmax, umax(a, b));
+                }
+                const u32 mm = st_mm[ent], cc = st_c[ent];
+                const u32 pmin = mm & 0xffffu, pmax = mm >> 16;
+                zmin = umin(pmin, rmin);
+                zmax = umax(pmax, rmax);
+                cmin = zmin == pmin ? (cc & 0xffu) : 0u;
+                cmax = zmax == pmax ? (cc >> 8) : 0u;
+#pragma unroll 4
+                for (int dx = -R; dx <= R; ++dx) {
+                    const u32 a = top[dx], b = bot[dx];
+                    cmin += (a == zmin) + (b == zmin);
+                    cmax += (a == zmax) + (b == zmax);
+                }
+#pragma unroll 4
+                for (int dy = 1 - R; dy < R; ++dy) {
+                    const u32 a = ctr[dy * g.GS - R], b = ctr[dy * g.GS + R];
+                    cmin += (a == zmin) + (b == zmin);
+                    cmax += (a == zmax) + (b == zmax);
                 }
             }
             if (cmin <= (u32)M0 && cmax <= (u32)M0) {
-                if (zmin < zxy && zxy < zmax) fs[r * FS + c] = (u16)zxy;
-                else to_sel = true;
+                if (zmin < zxy && zxy < zmax) {
+                    fs[r * FS + c] = (u16)zxy;
+                } else {
+                    to_sel = true;
+                    if (K > 5) st_mm[ent] = zmin | (zmax << 16);
+                }
             } else if (last) {
                 fs[r * FS + c] = (u16)(keep ? zxy : (cmin > (u32)M0 ? zmin : zmax));
             } else {
                 to_next = true;
+                // counts reach at most K*K <= 169 before the last window
+                st_mm[ent] = zmin | (zmax << 16);
+                st_c[ent] = (u16)(cmin | (cmax << 8));
             }
         }
         const u32 bn = __ballot_sync(FULL, to_next), bs_ = __ballot_sync(FULL, to_sel);
@@ -585,38 +631,83 @@ __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur,
     }
 }
 
+// Medians of the K x K windows of the nsel pixels on the selection list
+// (stored downward from sel_top).  K = 5: forgetful selection, one thread per
+// pixel.  K >= 7: G lanes per pixel (G a power of two, more when the list is
+// short) split the window rows; each pass counts c = #{v <= t} at the bracket
+// midpoint t and also finds max{v <= t} and min{v > t}, so the bracket
+// [lo, hi] (lo <= median <= hi, starting inside (zmin, zmax)) moves onto
+// sample values: c > (K*K-1)/2 puts the median at or below max{v <= t},
+// otherwise at or above min{v > t}.  Ends when lo == hi: the exact median.
 template <int K>
-__device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel)
+__device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel, const u32 *st_mm)
 {
-    constexpr int R = K / 2;
-    for (int e = threadIdx.x; e < nsel; e += kThreads) {
-        const u32 ent = *(sel_top - e);
-        const int r = (int)(ent >> 6), c = (int)(ent & 63u);
-        const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
-        u32 zmed;
-        if (K == 5) {
-            zmed = median25(ctr, g.GS);
-        } else {
-            u32 zmin = 0xffffu, zmax = 0u;
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    if (K == 5) {
+        for (int e = threadIdx.x; e < nsel; e += kThreads) {
+            const u32 ent = *(sel_top - e);
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            fs[r * FS + c] = (u16)median25(gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa), g.GS);
+        }
+        return;
+    }
+    constexpr int GMAX = K >= 9 ? 8 : 4;
+    int G = 1;
+    while (G < GMAX && nsel * G * 2 <= kThreads) G *= 2;
+    const int gid = threadIdx.x / G, gl = threadIdx.x & (G - 1), ngroups = kThreads / G;
+    const int rounds = (nsel + ngroups - 1) / ngroups;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int e = rd * ngroups + gid;
+        const bool valid = e < nsel;
+        u32 ent = 0, lo = 1, hi = 0;
+        const u16 *ctr = gs;
+        if (valid) {
+            ent = *(sel_top - e);
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
+            const u32 mm = st_mm[ent];
+            lo = (mm & 0xffffu) + 1u;
+            hi = (mm >> 16) - 1u;
+        }
+        // every lane of the warp runs the same number of passes (shuffles)
+        while (__any_sync(FULL, lo < hi)) {
+            const bool act = lo < hi;
+            const u32 t = (lo + hi) >> 1;
+            u32 cnt = 0, below = 0, above = 0xffffu;
+            if (act) {
 #pragma unroll 1
-            for (int dy = -R; dy <= R; ++dy) {
-                const u16 *row = ctr + dy * g.GS;
+                for (int dy = gl - R; dy <= R; dy += G) {
+                    const u16 *row = ctr + dy * g.GS;
 #pragma unroll
-                for (int dx = -R; dx <= R; ++dx) {
-                    const u32 v = row[dx];
-                    zmin = umin(zmin, v);
-                    zmax = umax(zmax, v);
+                    for (int dx = -R; dx <= R; ++dx) {
+                        const u32 v = row[dx];
+                        const bool le = v <= t;
+                        cnt += le;
+                        below = umax(below, le ? v : 0u);
+                        above = umin(above, le ? 0xffffu : v);
+                    }
                 }
             }
-            zmed = median_bisect<K>(ctr, g.GS, zmin, zmax);
+            for (int m = 1; m < G; m <<= 1) {
+                cnt += __shfl_xor_sync(FULL, cnt, m);
+                below = umax(below, __shfl_xor_sync(FULL, below, m));
+                above = umin(above, __shfl_xor_sync(FULL, above, m));
+            }
+            if (act) {
+                if (cnt > (u32)M0) hi = below;
+                else lo = above;
+            }
         }
-        fs[r * FS + c] = (u16)zmed;
+        if (valid && gl == 0) {
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            fs[r * FS + c] = (u16)lo;
+        }
     }
 }
 
 // Windows k = 5..Smax for the pixels that failed level A at k = 3.
 __device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl0, u16 *wl1, int *cnt,
-                         int cap)
+                         int cap, u32 *st_mm, u16 *st_c)
 {
     const bool keep = d.unresolved != 0;
     u16 *cur = wl0, *nxt = wl1;
@@ -631,24 +722,25 @@ __device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs,
         __syncthreads();
         const bool last = k == d.smax;
         switch (k) {
-        case 5: grow_level<5>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
-        case 7: grow_level<7>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
-        case 9: grow_level<9>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
-        case 11: grow_level<11>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
-        case 13: grow_level<13>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
-        default: grow_level<15>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep); break;
+        case 5: grow_level<5>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c); break;
+        case 7: grow_level<7>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c); break;
+        case 9: grow_level<9>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c); break;
+        case 11: grow_level<11>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c); break;
+        case 13: grow_level<13>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c); break;
+        default: grow_level<15>(g, gs, fs, cur, n, nxt, cap, &cnt[ci ^ 1], &cnt[2], last, keep, st_mm, st_c);
+            break;
         }
         __syncthreads();
         const int nsel = cnt[2];
         if (nsel > 0) {
             const u16 *top = nxt + cap - 1;
             switch (k) {
-            case 5: select_level<5>(g, gs, fs, top, nsel); break;
-            case 7: select_level<7>(g, gs, fs, top, nsel); break;
-            case 9: select_level<9>(g, gs, fs, top, nsel); break;
-            case 11: select_level<11>(g, gs, fs, top, nsel); break;
-            case 13: select_level<13>(g, gs, fs, top, nsel); break;
-            default: select_level<15>(g, gs, fs, top, nsel); break;
+            case 5: select_level<5>(g, gs, fs, top, nsel, st_mm); break;
+            case 7: select_level<7>(g, gs, fs, top, nsel, st_mm); break;
+            case 9: select_level<9>(g, gs, fs, top, nsel, st_mm); break;
+            case 11: select_level<11>(g, gs, fs, top, nsel, st_mm); break;
+            case 13: select_level<13>(g, gs, fs, top, nsel, st_mm); break;
+            default: select_level<15>(g, gs, fs, top, nsel, st_mm); break;
             }
             __syncthreads();
         }
@@ -806,13 +898,21 @@ struct BlockShared {
 };
 
 // ---------------------------------------------------------------- Wiener passes
+struct ApplyConst {
+    u32 n;
+    float v2f, inv_n, inv_n2, maxv;
+};
+
 // Phase-1 statistics of one tile: sum over its pixels of S1^2 (A) and of
-// M(q) f_q^2 (B); added to the image's exact sums.
-template <bool NARROW>
-__device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, BlockShared &bs)
+// M(q) f_q^2 (B), added to the image's exact sums.  With a plane, the tile's
+// binary32 mu = fl(S1)*fl(1/n) and s2 = fl(D)*fl(1/n^2) (neither depends on the
+// noise variance) are stored for phase 2, which then needs no sums and no halo.
+template <bool NARROW, bool PLANE>
+__device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, void *h2p, BlockShared &bs)
 {
     const int w = d.w;
-    hsums<NARROW>(g, fs, H1, nullptr, w, false);
+    constexpr bool with_plane = PLANE;
+    hsums<NARROW>(g, fs, H1, h2p, w, with_plane);
     const bool zero = d.border_zero != 0;
     const bool interior = !zero && g.y0 >= g.Rw && g.y0 + g.th <= d.H - g.Rw && g.x0 >= g.Rw &&
                           g.x0 + g.tw <= d.W - g.Rw;
@@ -830,11 +930,26 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     u64 accA = 0, accB = 0;
     if (x < g.tw && j0 < j1) {
         const bool two = x + 1 < g.tw;
-        u32 sa = 0, sb = 0;
+        const u32 n = (u32)(w * w);
+        const float inv_n = __frcp_rn((float)n), inv_n2 = __frcp_rn((float)(n * n));
+        const u32 *H2n = reinterpret_cast<const u32 *>(h2p);
+        const u64 *H2w = reinterpret_cast<const u64 *>(h2p);
+        u32 sa = 0, sb = 0, qa = 0, qb = 0;
+        u64 wa = 0, wb = 0;
         for (int t = 0; t < w; ++t) {
             const uint2 h = *reinterpret_cast<const uint2 *>(H1 + (j0 + t) * HS + x);
             sa += h.x;
             sb += h.y;
+            if (with_plane) {
+                if (NARROW) {
+                    const uint2 q = *reinterpret_cast<const uint2 *>(H2n + (j0 + t) * HS + x);
+                    qa += q.x;
+                    qb += q.y;
+                } else {
+                    wa += H2w[(j0 + t) * HS + x];
+                    wb += H2w[(j0 + t) * HS + x + 1];
+                }
+            }
         }
         for (int j = j0; j < j1; ++j) {
             const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
@@ -851,11 +966,37 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
                     accB += (u64)(fb * fb) * (my * bs.mx[x + 1]);
                 }
             }
+            if (with_plane) {
+                float da, db;
+                if (NARROW) {
+                    da = __uint2float_rn(n * qa - sa * sa);     // exact: the true value is < 2^32
+                    db = __uint2float_rn(n * qb - sb * sb);
+                } else {
+                    da = __ull2float_rn((u64)n * wa - (u64)sa * sa);
+                    db = __ull2float_rn((u64)n * wb - (u64)sb * sb);
+                }
+                float2 *pp = reinterpret_cast<float2 *>(d.plane) + (long long)(g.y0 + j) * d.W + g.x0 + x;
+                pp[0] = make_float2(__fmul_rn(__uint2float_rn(sa), inv_n), __fmul_rn(da, inv_n2));
+                if (two) pp[1] = make_float2(__fmul_rn(__uint2float_rn(sb), inv_n), __fmul_rn(db, inv_n2));
+            }
             if (j + 1 < j1) {
                 const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
                 const uint2 ho_ = *reinterpret_cast<const uint2 *>(H1 + j * HS + x);
                 sa += hi_.x - ho_.x;
                 sb += hi_.y - ho_.y;
+                if (with_plane) {
+                    if (NARROW) {
+                        const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + w) * HS + x);
+                        const uint2 qo = *reinterpret_cast<const uint2 *>(H2n + j * HS + x);
+                        qa += qi.x - qo.x;
+                        qb += qi.y - qo.y;
+                    } else {
+                        wa += H2w[(j + w) * HS + x];
+                        wa -= H2w[j * HS + x];
+                        wb += H2w[(j + w) * HS + x + 1];
+                        wb -= H2w[j * HS + x + 1];
+                    }
+                }
             }
         }
     }
@@ -875,17 +1016,12 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         }
         split_add(&d.ctl->A_lo32, &d.ctl->A_hi32, sa);
         split_add(&d.ctl->B_lo32, &d.ctl->B_hi32, sb);
-        // release: the CTA's f tile (ordered before this thread by the barrier)
-        // and the sums become visible before the done count
+        // release: the CTA's f tile and plane (ordered before this thread by
+        // the barrier) and the sums become visible before the done count
         __threadfence();
         atomicAdd(&d.ctl->p1_done, 1u);
     }
 }
-
-struct ApplyConst {
-    u32 n;
-    float v2f, inv_n, inv_n2, maxv;
-};
 
 // binary32 Wiener output of one pixel (fixed evaluation order, see top).
 __device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyConst &k, float &y)
@@ -895,7 +1031,9 @@ __device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyC
     const float den = fmaxf(s2, k.v2f);
     const float num = fmaxf(__fsub_rn(s2, k.v2f), 0.0f);
     if (den > 0.0f) {
-        const float gain = __fdiv_rn(num, den);
+        // num = 0 (local variance at or below the noise level, most pixels of
+        // flat areas) gives gain = +0 exactly; skip the divide there
+        const float gain = num > 0.0f ? __fdiv_rn(num, den) : 0.0f;
         y = __fadd_rn(mu, __fmul_rn(gain, __fsub_rn(__uint2float_rn(fv), mu)));
     } else {
         y = mu;
@@ -903,6 +1041,104 @@ __device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyC
     float q = floorf(__fadd_rn(y, 0.5f));
     q = fminf(fmaxf(q, 0.0f), k.maxv);
     return (u32)q;
+}
+
+// binary32 Wiener output from the stored (mu, s2) of a pixel.
+__device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const ApplyConst &k, float &y)
+{
+    const float den = fmaxf(s2, k.v2f);
+    const float num = fmaxf(__fsub_rn(s2, k.v2f), 0.0f);
+    if (den > 0.0f) {
+        // num = 0 (local variance at or below the noise level, most pixels of
+        // flat areas) gives gain = +0 exactly; skip the divide there
+        const float gain = num > 0.0f ? __fdiv_rn(num, den) : 0.0f;
+        y = __fadd_rn(mu, __fmul_rn(gain, __fsub_rn(__uint2float_rn(fv), mu)));
+    } else {
+        y = mu;
+    }
+    float q = floorf(__fadd_rn(y, 0.5f));
+    q = fminf(fmaxf(q, 0.0f), k.maxv);
+    return (u32)q;
+}
+
+// Phase-2 apply from the plane: a streaming pass over the tile's own pixels
+// (no halo, no sums), two pixels per lane, stored as one pixel pair.  Each
+// warp takes up to kRows rows per round and issues all their loads before
+// any store, so the loads of a round are in flight together.
+__device__ __forceinline__ void store_pair(uint8_t *px, int elem, bool two, u32 oa, u32 ob)
+{
+    if (elem == 1) {
+        if (two && (reinterpret_cast<uintptr_t>(px) & 1) == 0) {
+            *reinterpret_cast<u16 *>(px) = (u16)(oa | (ob << 8));
+        } else {
+            px[0] = (uint8_t)oa;
+            if (two) px[1] = (uint8_t)ob;
+        }
+    } else {
+        if (two && (reinterpret_cast<uintptr_t>(px) & 3) == 0) {
+            *reinterpret_cast<u32 *>(px) = oa | (ob << 16);
+        } else {
+            reinterpret_cast<u16 *>(px)[0] = (u16)oa;
+            if (two) reinterpret_cast<u16 *>(px)[1] = (u16)ob;
+        }
+    }
+}
+
+__device__ void tile_apply_plane(const ImgDesc &d, const Geo &g, const uint8_t *fsrc, long long fpitch, float v2f)
+{
+    constexpr int kRows = 4;
+    ApplyConst k;
+    k.n = 0;
+    k.v2f = v2f;
+    k.inv_n = 0.f;
+    k.inv_n2 = 0.f;
+    k.maxv = (float)d.maxv;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = 2 * lane;
+    if (x >= g.tw) return;
+    const bool two = x + 1 < g.tw;
+    const float2 *plane = reinterpret_cast<const float2 *>(d.plane) + g.x0 + x;
+    const uint8_t *fcol = fsrc + (long long)(g.x0 + x) * d.elem;
+    for (int j0 = warp; j0 < g.th; j0 += kWarps * kRows) {
+        float2 ma[kRows], mb[kRows];
+        u32 fa[kRows], fb[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int j = j0 + r * kWarps;
+            ma[r] = mb[r] = make_float2(0.f, 0.f);
+            fa[r] = fb[r] = 0;
+            if (j < g.th) {
+                const long long y = g.y0 + j;
+                const float2 *pp = plane + y * d.W;
+                ma[r] = __ldcg(pp);
+                if (two) mb[r] = __ldcg(pp + 1);
+                const uint8_t *fr = fcol + y * fpitch;
+                if (d.elem == 1) {
+                    fa[r] = __ldcg(fr);
+                    if (two) fb[r] = __ldcg(fr + 1);
+                } else {
+                    fa[r] = __ldcg(reinterpret_cast<const u16 *>(fr));
+                    if (two) fb[r] = __ldcg(reinterpret_cast<const u16 *>(fr) + 1);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int j = j0 + r * kWarps;
+            if (j < g.th) {
+                const long long y = g.y0 + j;
+                float ya, yb = 0.f;
+                const u32 oa = wiener_ms(ma[r].x, ma[r].y, fa[r], k, ya);
+                const u32 ob = two ? wiener_ms(mb[r].x, mb[r].y, fb[r], k, yb) : 0u;
+                store_pair(d.dst + y * d.dst_pitch + (long long)(g.x0 + x) * d.elem, d.elem, two, oa, ob);
+                if (d.y_out) {
+                    float *yp = d.y_out + y * d.W + g.x0 + x;
+                    yp[0] = ya;
+                    if (two) yp[1] = yb;
+                }
+            }
+        }
+    }
 }
 
 // Wiener apply of one tile: vertical sliding sums of H1, H2 per column pair,
@@ -1000,6 +1236,8 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
 // ---------------------------------------------------------------- one work item
 struct Views {
     u16 *fs, *gs, *wl0, *wl1;
+    u32 *st_mm;
+    u16 *st_c;
     u32 *h1;
     void *h2;
 };
@@ -1068,11 +1306,31 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     const bool do_amf = phase == 1 && mode_median(mode);
     HD_STAMP_INIT();
 
+    const bool est = mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST;
+    if (phase == 2 && d.plane) {
+        // streaming apply from the plane: no f region needed
+        if (threadIdx.x == 0) {
+            if (bs.nu2_of != d.ctl) {
+                const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
+                bs.nu2 = nu2;
+                bs.nu2f = __double2float_rn(nu2);
+                bs.nu2_of = d.ctl;
+            }
+            if (g.x0 == 0 && g.y0 == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
+        }
+        __syncthreads();
+        if (mode == MODE_HYBRID_EST) tile_apply_plane(d, g, d.fbuf, d.f_pitch, bs.nu2f);
+        else tile_apply_plane(d, g, d.src, d.src_pitch, bs.nu2f);
+        HD_STAMP(6);
+        return;
+    }
+
     // ---- the f region in shared memory
     if (do_amf) {
         if (threadIdx.x == 0) bs.cnt[0] = 0;
-        load_region(vw.gs + g.pa, g.GS, g.nrow + 2 * g.Ra, g.ncol + 2 * g.Ra, d.src, d.src_pitch, d.elem, d.H, d.W,
-                    g.gfy - g.Ra, g.gfx - g.Ra, false, false);
+        load_region<false>(vw.gs + g.pa, g.GS, g.nrow + 2 * g.Ra, g.ncol + 2 * g.Ra, d.src, d.src_pitch, d.elem,
+                           d.H, d.W, g.gfy - g.Ra, g.gfx - g.Ra, false,
+                           d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem);
         // the next ticket (taken when this item started) has arrived by now
         if (lp.ticket && threadIdx.x == 0) bs.item[2] = next;
         __syncthreads();
@@ -1082,7 +1340,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         else amf3_scalar(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
         __syncthreads();
         HD_STAMP(1);
-        if (d.smax > 3) amf_grow(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW);
+        if (d.smax > 3) amf_grow(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW, vw.st_mm, vw.st_c);
         if (g.Rw > 0 && d.border_zero) {
             // zero-border Wiener: samples outside the image read 0
             for (int i = threadIdx.x; i < g.nrow * g.ncol; i += kThreads) {
@@ -1093,9 +1351,13 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         }
         __syncthreads();
     } else {
-        const bool from_f = (phase == 2 && mode == MODE_HYBRID_EST);
-        load_region(vw.fs, FS, g.nrow, g.ncol, from_f ? d.fbuf : d.src, from_f ? d.f_pitch : d.src_pitch, d.elem,
-                    d.H, d.W, g.gfy, g.gfx, d.border_zero != 0, from_f);
+        if (phase == 2 && mode == MODE_HYBRID_EST)
+            load_region<true>(vw.fs, FS, g.nrow, g.ncol, d.fbuf, d.f_pitch, d.elem, d.H, d.W, g.gfy, g.gfx,
+                              d.border_zero != 0, d.fbuf + (long long)d.H * d.f_pitch);
+        else
+            load_region<false>(vw.fs, FS, g.nrow, g.ncol, d.src, d.src_pitch, d.elem, d.H, d.W, g.gfy, g.gfx,
+                               d.border_zero != 0,
+                               d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem);
         __syncthreads();
         HD_STAMP(5);
     }
@@ -1109,15 +1371,15 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         store_region(vw.fs + g.Rw * FS + g.Lm, FS, g.th, g.tw, d.fbuf, d.f_pitch, d.elem, g.y0, g.x0);
         HD_STAMP(3);
     }
-    if (phase == 1 && (mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST)) {
-        tile_stats<NARROW>(d, g, vw.fs, vw.h1, bs);
+    if (phase == 1 && est) {
+        if (d.plane) tile_stats<NARROW, true>(d, g, vw.fs, vw.h1, vw.h2, bs);
+        else tile_stats<NARROW, false>(d, g, vw.fs, vw.h1, vw.h2, bs);
         HD_STAMP(4);
         return;
     }
     // one thread converts the noise variance (binary64 is slow here); the
     // value is cached per CTA for the image's following tiles
     if (threadIdx.x == 0) {
-        const bool est = mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST;
         if (!est || bs.nu2_of != d.ctl) {
             const u64 n = (u64)d.w * (u64)d.w;
             const double nu2 = est ? noise_variance(d.ctl, n, d.H, d.W) : d.noise_var;
@@ -1182,6 +1444,8 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
     vw.gs = reinterpret_cast<u16 *>(smem_raw + L.gs);
     vw.wl0 = reinterpret_cast<u16 *>(smem_raw + L.wl);
     vw.wl1 = vw.wl0 + lp.region_h * FW;
+    vw.st_mm = reinterpret_cast<u32 *>(smem_raw + L.st);
+    vw.st_c = reinterpret_cast<u16 *>(smem_raw + L.st + (size_t)lp.region_h * FW * sizeof(u32));
     vw.h1 = reinterpret_cast<u32 *>(smem_raw + L.h1);
     vw.h2 = smem_raw + L.h2;
 

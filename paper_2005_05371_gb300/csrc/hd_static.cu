@@ -5,8 +5,9 @@
 // cudaMalloc is not allowed or would block (inside a real-time frame loop
 // with a fixed memory budget, in a plug-in host that owns the CUDA
 // allocator, or in a driver-side callback).  For them the scratch this
-// path needs (the median-filtered plane kept between the two phases, and the
-// work-queue counters) lives in one fixed array in device memory, declared
+// path needs (the median-filtered plane kept between the two phases, the
+// work-queue counters and, when it fits, the plane of binary32 local
+// statistics) lives in one fixed array in device memory, declared
 // below.  Every GPU that loads this library holds that array until the
 // process exits.
 #include <cuda_runtime.h>
@@ -52,7 +53,8 @@ extern "C" hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stre
     if (!img) return HD_ERR_ARG;
     if (img->H < 1 || img->W < 1) return HD_ERR_ARG;
     size_t need = 0;
-    hd_status st = hybrid_workspace_size(img->H, img->W, img->dtype, &img->p, &need);
+    // the smallest workspace is enough; the (mu, s2) plane is used when it fits too
+    hd_status st = hybrid_min_workspace_size(img->H, img->W, img->dtype, &img->p, &need);
     if (st != HD_OK) return st;
     if (need > HD_STATIC_SCRATCH_BYTES) return HD_ERR_OVERFLOW;
     void *scratch = nullptr;

@@ -91,16 +91,20 @@ def test_workspace_checks_before_launch():
     img = _img()
     assert call("hybrid_denoise", img, None, 0) == hd.HD_ERR_WORKSPACE
     assert call("hybrid_denoise", img, 0x1000 + 8, 1 << 20) == hd.HD_ERR_WORKSPACE   # misaligned
-    need = hd.hybrid_workspace_size(16, 16, hd.HD_U8, hd.Params(5, 3))
+    need = hd.hybrid_min_workspace_size(16, 16, hd.HD_U8, hd.Params(5, 3))
     assert call("hybrid_denoise", img, 0x10000, need - 1) == hd.HD_ERR_WORKSPACE
 
 
 def test_workspace_sizes():
     p = hd.Params(11, 5)
-    n8 = hd.hybrid_workspace_size(1620, 1620, hd.HD_U8, p)
-    n16 = hd.hybrid_workspace_size(4096, 4096, hd.HD_U16, p)
+    n8 = hd.hybrid_min_workspace_size(1620, 1620, hd.HD_U8, p)
+    n16 = hd.hybrid_min_workspace_size(4096, 4096, hd.HD_U16, p)
     assert n8 >= 1620 * 1620 and n8 < 1620 * 1620 + 64 * 1024
     assert n16 >= 4096 * 4096 * 2 and n16 < 4096 * 4096 * 2 + 64 * 1024
+    # the full size adds the binary32 (mu, sigma2) plane: 8 bytes per pixel
+    f8 = hd.hybrid_workspace_size(1620, 1620, hd.HD_U8, p)
+    assert f8 - n8 >= 8 * 1620 * 1620 and f8 - n8 < 8 * 1620 * 1620 + 512
+    assert hd.hybrid_min_workspace_size(512, 512, hd.HD_U8, hd.Params(7, 3, noise_var=25.0)) == 0
     # a supplied noise variance makes the hybrid one pass: no workspace
     assert hd.hybrid_workspace_size(512, 512, hd.HD_U8, hd.Params(7, 3, noise_var=25.0)) == 0
     assert hd.wiener_workspace_size(512, 512, hd.HD_U8, hd.Params(7, 3)) > 0

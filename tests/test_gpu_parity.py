@@ -71,24 +71,50 @@ def gpu_amf(g, smax, unresolved=0, pad=0, bits=None):
     return to_host(dst, g.dtype)
 
 
-def gpu_hybrid(g, smax, w, noise_var=-1.0, border=0, unresolved=0, bits=None, pad=0, want_y=False):
+def exact_workspace(n):
+    """A zeroed workspace whose usable length (after 256-byte alignment) is exactly n."""
+    buf = hd._workspace(n, DEV)
+    p = buf.data_ptr()
+    return buf[:(p + 255) // 256 * 256 - p + n]
+
+
+def min_workspace(H, W, code, p):
+    """A workspace of the least accepted size (no statistics plane)."""
+    n = hd.hybrid_min_workspace_size(H, W, code, p)
+    return exact_workspace(n) if n else None
+
+
+def gpu_hybrid(g, smax, w, noise_var=-1.0, border=0, unresolved=0, bits=None, pad=0, want_y=False,
+               minimal=False):
     src = to_dev(g, pad)
     dst = empty_like_dev(g, pad)
     nv = torch.full((1,), -7.0, dtype=torch.float64, device=DEV)
     y = torch.empty(g.shape, dtype=torch.float32, device=DEV) if want_y else None
+    ws = None
+    if minimal:
+        code = hd.HD_U8 if g.dtype == np.uint8 else hd.HD_U16
+        b = bits if bits is not None else (8 if g.dtype == np.uint8 else 16)
+        ws = min_workspace(*g.shape, code, hd.Params(smax, w, noise_var=noise_var, bits=b))
     hd.hybrid_denoise(src, dst, smax=smax, wiener_w=w, noise_var=noise_var, border=border,
-                      unresolved=unresolved, bits=bits, noise_var_out=nv, y_out=y)
+                      unresolved=unresolved, bits=bits, noise_var_out=nv, y_out=y, workspace=ws)
     assert hd.hd_get_device_error() == hd.HD_OK
     return to_host(dst, g.dtype), float(nv.item()), (y.cpu().numpy() if want_y else None)
 
 
-def gpu_wiener(f, w, noise_var=-1.0, border=0, bits=None, pad=0):
+def gpu_wiener(f, w, noise_var=-1.0, border=0, bits=None, pad=0, minimal=False):
     src = to_dev(f, pad)
     dst = empty_like_dev(f, pad)
     nv = torch.full((1,), -7.0, dtype=torch.float64, device=DEV)
     y = torch.empty(f.shape, dtype=torch.float32, device=DEV)
+    ws = None
+    if minimal and noise_var < 0:
+        # the full size less the 8-byte-per-pixel statistics plane (256-byte rounded)
+        code = hd.HD_U8 if f.dtype == np.uint8 else hd.HD_U16
+        b = bits if bits is not None else (8 if f.dtype == np.uint8 else 16)
+        full = hd.wiener_workspace_size(*f.shape, code, hd.Params(3, w, noise_var=noise_var, bits=b))
+        ws = exact_workspace(full - (8 * f.shape[0] * f.shape[1] + 255) // 256 * 256)
     hd.wiener_filter(src, dst, wiener_w=w, noise_var=noise_var, border=border, bits=bits, noise_var_out=nv,
-                     y_out=y)
+                     y_out=y, workspace=ws)
     assert hd.hd_get_device_error() == hd.HD_OK
     return to_host(dst, f.dtype), float(nv.item()), y.cpu().numpy()
 
@@ -176,6 +202,31 @@ def test_hybrid_matches_oracle(shape, dtype, bits):
                 f, ref = oracle.hybrid(g, smax, w, noise_var=nv, bits=bits, border_zero=bool(border))
                 out, nu2, y = gpu_hybrid(g, smax, w, noise_var=nv, border=border, bits=bits, want_y=True)
                 check_wiener(out, nu2, y, ref, bits)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (31, 33), (33, 65), (130, 257)])
+@pytest.mark.parametrize("dtype,bits", [(np.uint8, 8), (np.uint16, 12), (np.uint16, 16)])
+def test_recompute_path_matches_oracle(shape, dtype, bits):
+    """With the least workspace (no statistics plane) the Wiener pass
+    recomputes the window sums; the output is the same as the oracle's."""
+    g = noisy_image(*shape, dtype, seed=5 * shape[0] + shape[1])
+    for smax, w in ((3, 3), (7, 5), (15, 15)):
+        for border in (0, 1):
+            f, ref = oracle.hybrid(g, smax, w, noise_var=-1.0, bits=bits, border_zero=bool(border))
+            out, nu2, y = gpu_hybrid(g, smax, w, border=border, bits=bits, want_y=True, minimal=True)
+            check_wiener(out, nu2, y, ref, bits)
+            ref_w = oracle.wiener(f, w, noise_var=-1.0, bits=bits, border_zero=bool(border))
+            out, nu2, y = gpu_wiener(f, w, border=border, bits=bits, minimal=True)
+            check_wiener(out, nu2, y, ref_w, bits)
+
+
+def test_plane_and_recompute_paths_identical():
+    spec, clean, g = synth.config_image("paper1620")
+    a = gpu_hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits, want_y=True)
+    b = gpu_hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits, want_y=True, minimal=True)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1]
+    np.testing.assert_array_equal(a[2], b[2])
 
 
 def test_hybrid_pitched_and_repeated_workspace():

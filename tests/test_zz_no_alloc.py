@@ -74,9 +74,27 @@ def test_static_mixed_sizes_and_given_noise_variance():
 
 def test_static_rejects_images_beyond_the_fixed_scratch():
     p = hd.Params(7, 5, bits=12)
-    need = hd.hybrid_workspace_size(4096, 4800, hd.HD_U16, p)
+    need = hd.hybrid_min_workspace_size(4096, 4800, hd.HD_U16, p)
     assert need > STATIC_BYTES
     src = torch.zeros((4096, 4800), dtype=torch.int16, device="cuda:0")
     dst = torch.empty_like(src)
     assert _call_static(src, dst, p) == hd.HD_ERR_OVERFLOW
-    assert hd.hybrid_workspace_size(4096, 4096, hd.HD_U16, p) <= STATIC_BYTES
+    assert hd.hybrid_min_workspace_size(4096, 4096, hd.HD_U16, p) <= STATIC_BYTES
+
+
+def test_static_large_image_takes_the_recompute_path():
+    """4096 x 4096 at 12 bits: the median plane fits the fixed array but the
+    statistics plane does not, so the Wiener pass recomputes its window sums;
+    the output still equals hybrid_denoise with its full workspace."""
+    p = hd.Params(7, 5, bits=12)
+    assert hd.hybrid_workspace_size(4096, 4096, hd.HD_U16, p) > STATIC_BYTES
+    rng = np.random.default_rng(77)
+    g = rng.integers(0, 4096, size=(4096, 4096)).astype(np.uint16)
+    g[rng.random(g.shape) < 0.2] = 4095
+    src = _dev(g)
+    ref = torch.empty_like(src)
+    hd.hybrid_denoise(src, ref, 7, 5, bits=12)
+    out = torch.empty_like(src)
+    assert _call_static(src, out, p) == hd.HD_OK
+    torch.testing.assert_close(out, ref, rtol=0, atol=0)
+    assert hd.hd_get_device_error() == hd.HD_OK
