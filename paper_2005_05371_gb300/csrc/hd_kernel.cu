@@ -56,6 +56,7 @@
 // binary64 conversion, computed by one thread per CTA and image (binary64 is
 // slow on this part).
 #include <cuda_runtime.h>
+#include <climits>
 #include <cstdint>
 #include <cstring>
 #include "hd_internal.h"
@@ -97,6 +98,11 @@ constexpr u32 FULL = 0xffffffffu;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline int g_stride(int ra) { return FW + 2 * ra + 4; }
+// One phase-2 stage: the unit's (mu, s2) pairs, then its f bytes as up to two
+// row segments widened to 16-byte boundaries.
+constexpr int kStagePlane = kUnitPx * 8;
+constexpr int kStageBytes = kStagePlane + kUnitPx * 2 + 64;
+static_assert(kStageBytes % 16 == 0, "stage alignment");
 
 struct SmemLayout {
     size_t fs, gs, wl, st, h1, h2, total;
@@ -124,6 +130,8 @@ __host__ __device__ inline SmemLayout layout(int FH, int ra_max, int wide)
     L.h2 = b;
     b = align16(b + (size_t)FH * HS * (wide ? sizeof(u64) : sizeof(u32)));
     L.total = a > b ? a : b;
+    // plane-mode phase 2 stages its units over the whole area
+    if (L.total < (size_t)kStages * kStageBytes) L.total = (size_t)kStages * kStageBytes;
     return L;
 }
 
@@ -885,8 +893,18 @@ __device__ bool wait_phase1(const ImgDesc &d, u32 total, u64 limit, int *s_flag)
     return *s_flag != 0;
 }
 
+struct P2Stage {
+    int unit;         // staged unit, or the unit count when the stage is empty
+    int y0, x0;       // first pixel of the unit
+    int na;           // pixels of the unit in row y0
+    int fa, fb;       // stage offsets of f for row y0 and row y0 + 1 (-1: f not staged)
+};
+
 struct BlockShared {
     int item[3];      // current / next ticket (double buffer), next ticket for the prefetch
+    u64 full[kStages];        // plane-mode phase 2: stage s staged (bulk-copy bytes landed)
+    P2Stage st[kStages];      //   what each stage holds
+    u32 fullpar;              //   bit s: parity of the next phase to wait for on stage s
     const ImgCtl *nu2_of;   // image whose noise variance is cached below
     double nu2;
     float nu2f;
@@ -1030,10 +1048,11 @@ __device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyC
     const float s2 = __fmul_rn(dfl, k.inv_n2);
     const float den = fmaxf(s2, k.v2f);
     const float num = fmaxf(__fsub_rn(s2, k.v2f), 0.0f);
-    if (den > 0.0f) {
-        // num = 0 (local variance at or below the noise level, most pixels of
-        // flat areas) gives gain = +0 exactly; skip the divide there
-        const float gain = num > 0.0f ? __fdiv_rn(num, den) : 0.0f;
+    // num = 0 (local variance at or below the noise level: most pixels of flat
+    // areas, and every pixel with den = 0) gives gain = +0 and y = mu + (+-0)
+    // = mu exactly (mu >= +0); only num > 0 (then den >= num) needs the divide
+    if (num > 0.0f) {
+        const float gain = __fdiv_rn(num, den);
         y = __fadd_rn(mu, __fmul_rn(gain, __fsub_rn(__uint2float_rn(fv), mu)));
     } else {
         y = mu;
@@ -1048,10 +1067,11 @@ __device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const Apply
 {
     const float den = fmaxf(s2, k.v2f);
     const float num = fmaxf(__fsub_rn(s2, k.v2f), 0.0f);
-    if (den > 0.0f) {
-        // num = 0 (local variance at or below the noise level, most pixels of
-        // flat areas) gives gain = +0 exactly; skip the divide there
-        const float gain = num > 0.0f ? __fdiv_rn(num, den) : 0.0f;
+    // num = 0 (local variance at or below the noise level: most pixels of flat
+    // areas, and every pixel with den = 0) gives gain = +0 and y = mu + (+-0)
+    // = mu exactly (mu >= +0); only num > 0 (then den >= num) needs the divide
+    if (num > 0.0f) {
+        const float gain = __fdiv_rn(num, den);
         y = __fadd_rn(mu, __fmul_rn(gain, __fsub_rn(__uint2float_rn(fv), mu)));
     } else {
         y = mu;
@@ -1061,82 +1081,208 @@ __device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const Apply
     return (u32)q;
 }
 
-// Phase-2 apply from the plane: a streaming pass over the tile's own pixels
-// (no halo, no sums), two pixels per lane, stored as one pixel pair.  Each
-// warp takes up to kRows rows per round and issues all their loads before
-// any store, so the loads of a round are in flight together.
-__device__ __forceinline__ void store_pair(uint8_t *px, int elem, bool two, u32 oa, u32 ob)
+// ---------------------------------------------------------------- plane-mode phase 2
+// Units of kUnitPx pixels are staged in shared memory by bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per stage) up to kStages
+// units ahead of the one being applied.  Thread 0 claims units from
+// ctl->p2_next and issues the copies; all threads apply; a block barrier per
+// unit frees its stage for the next copy.
+__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64 *m, u32 count)
 {
-    if (elem == 1) {
-        if (two && (reinterpret_cast<uintptr_t>(px) & 1) == 0) {
-            *reinterpret_cast<u16 *>(px) = (u16)(oa | (ob << 8));
-        } else {
-            px[0] = (uint8_t)oa;
-            if (two) px[1] = (uint8_t)ob;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u64 *m)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(m)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u64 *m, u32 bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64 *m, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(m)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier.
+__device__ bool mbar_wait(u64 *m, u32 parity, u64 limit)
+{
+    for (u64 i = 0;; ++i) {
+        if (mbar_try_wait(m, parity)) return true;
+        if (i >= limit) return false;
+        if (i >= 64) __nanosleep(256);
+    }
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, u32 bytes, u64 *m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+
+// Thread 0: stage unit `unit` of image d into stage s.  Every address and
+// size is a multiple of 16 bytes and stays inside its buffer: the plane is
+// allocated in whole 256-byte blocks, f rows have a 16-byte-multiple pitch.
+__device__ void p2_issue(const ImgDesc &d, int unit, int s, unsigned char *stages, P2Stage *st, u64 *full)
+{
+    const u32 HW = (u32)d.H * (u32)d.W;
+    const u32 q0 = (u32)unit * (u32)kUnitPx;
+    const u32 n = min((u32)kUnitPx, HW - q0);
+    // row of q0: a binary32 estimate (off by at most one) corrected exactly
+    const u32 W = (u32)d.W;
+    u32 y0 = (u32)__fmul_rz((float)q0, __frcp_rz((float)W));
+    y0 = min(y0, (u32)d.H - 1u);
+    while (y0 > 0 && y0 * W > q0) --y0;
+    while ((y0 + 1u) * W <= q0) ++y0;
+    const u32 x0 = q0 - y0 * W;
+    const u32 na = min(n, W - x0);
+    unsigned char *sb = stages + (size_t)s * kStageBytes;
+    P2Stage &t = st[s];
+    t.unit = unit;
+    t.y0 = (int)y0;
+    t.x0 = (int)x0;
+    t.na = (int)na;
+    t.fa = t.fb = -1;
+    const u32 pbytes = (n * 8u + 15u) & ~15u;
+    u32 abytes = 0, bbytes = 0;
+    uintptr_t a0 = 0, b0 = 0;
+    if (d.mode == MODE_HYBRID_EST && n - na <= (u32)d.W) {
+        const uintptr_t ra = reinterpret_cast<uintptr_t>(d.fbuf + (size_t)y0 * d.f_pitch + (size_t)x0 * d.elem);
+        a0 = ra & ~uintptr_t(15);
+        abytes = (u32)(((ra + (size_t)na * d.elem + 15) & ~uintptr_t(15)) - a0);
+        t.fa = kStagePlane + (int)(ra - a0);
+        if (n > na) {
+            b0 = reinterpret_cast<uintptr_t>(d.fbuf + (size_t)(y0 + 1) * d.f_pitch);
+            bbytes = ((n - na) * (u32)d.elem + 15u) & ~15u;
+            t.fb = kStagePlane + (int)abytes;
         }
+    }
+    mbar_expect_tx(&full[s], pbytes + abytes + bbytes);
+    bulk_copy(sb, d.plane + 2 * (size_t)q0, pbytes, &full[s]);
+    if (abytes) bulk_copy(sb + kStagePlane, reinterpret_cast<const void *>(a0), abytes, &full[s]);
+    if (bbytes) bulk_copy(sb + kStagePlane + abytes, reinterpret_cast<const void *>(b0), bbytes, &full[s]);
+}
+
+// Unit claims of one slot (thread 0): a first block of the slot's share,
+// then one at a time, each claimed a unit ahead of its use.
+struct P2Claim {
+    int blk, blk_left, spare;
+};
+
+__device__ __forceinline__ int p2_next_unit(const ImgDesc &d, P2Claim &c)
+{
+    if (c.blk_left > 0) {
+        --c.blk_left;
+        return c.blk++;
+    }
+    const int u = c.spare >= 0 ? c.spare : (int)atomicAdd(&d.ctl->p2_next, 1u);
+    c.spare = (int)atomicAdd(&d.ctl->p2_next, 1u);
+    return u;
+}
+
+// Row and column of pixel j of a unit (j >= na: the following rows).
+__device__ __forceinline__ void unit_pixel(const ImgDesc &d, const P2Stage &t, u32 j, u32 &y, u32 &x)
+{
+    if (j < (u32)t.na) {
+        y = (u32)t.y0;
+        x = (u32)t.x0 + j;
     } else {
-        if (two && (reinterpret_cast<uintptr_t>(px) & 3) == 0) {
-            *reinterpret_cast<u32 *>(px) = oa | (ob << 16);
+        const u32 r = j - (u32)t.na;
+        if (r < (u32)d.W) {
+            y = (u32)t.y0 + 1;
+            x = r;
         } else {
-            reinterpret_cast<u16 *>(px)[0] = (u16)oa;
-            if (two) reinterpret_cast<u16 *>(px)[1] = (u16)ob;
+            y = (u32)t.y0 + 1 + r / (u32)d.W;
+            x = r % (u32)d.W;
         }
     }
 }
 
-__device__ void tile_apply_plane(const ImgDesc &d, const Geo &g, const uint8_t *fsrc, long long fpitch, float v2f)
+// All threads: apply the staged unit (four pixels a thread).
+__device__ void p2_apply(const ImgDesc &d, const unsigned char *sb, const P2Stage &t, float v2f)
 {
-    constexpr int kRows = 4;
+    const u32 HW = (u32)d.H * (u32)d.W;
+    const u32 q0 = (u32)t.unit * (u32)kUnitPx;
+    const u32 n = min((u32)kUnitPx, HW - q0);
+    const u32 j0 = threadIdx.x * 4u;
+    if (j0 >= n) return;
+    const int npx = (int)min(4u, n - j0);
     ApplyConst k;
     k.n = 0;
     k.v2f = v2f;
     k.inv_n = 0.f;
     k.inv_n2 = 0.f;
     k.maxv = (float)d.maxv;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x = 2 * lane;
-    if (x >= g.tw) return;
-    const bool two = x + 1 < g.tw;
-    const float2 *plane = reinterpret_cast<const float2 *>(d.plane) + g.x0 + x;
-    const uint8_t *fcol = fsrc + (long long)(g.x0 + x) * d.elem;
-    for (int j0 = warp; j0 < g.th; j0 += kWarps * kRows) {
-        float2 ma[kRows], mb[kRows];
-        u32 fa[kRows], fb[kRows];
+    const float4 *pp = reinterpret_cast<const float4 *>(sb) + 2 * threadIdx.x;
+    const float4 m01 = pp[0], m23 = pp[1];
+    const float mu[4] = {m01.x, m01.z, m23.x, m23.z};
+    const float s2[4] = {m01.y, m01.w, m23.y, m23.w};
+    const bool same_row = j0 + 3u < (u32)t.na || (j0 >= (u32)t.na && j0 + 3u - (u32)t.na < (u32)d.W);
+    u32 fv[4], ov[4];
+    float yv[4];
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const int j = j0 + r * kWarps;
-            ma[r] = mb[r] = make_float2(0.f, 0.f);
-            fa[r] = fb[r] = 0;
-            if (j < g.th) {
-                const long long y = g.y0 + j;
-                const float2 *pp = plane + y * d.W;
-                ma[r] = __ldcg(pp);
-                if (two) mb[r] = __ldcg(pp + 1);
-                const uint8_t *fr = fcol + y * fpitch;
-                if (d.elem == 1) {
-                    fa[r] = __ldcg(fr);
-                    if (two) fb[r] = __ldcg(fr + 1);
-                } else {
-                    fa[r] = __ldcg(reinterpret_cast<const u16 *>(fr));
-                    if (two) fb[r] = __ldcg(reinterpret_cast<const u16 *>(fr) + 1);
-                }
+    for (int i = 0; i < 4; ++i) {
+        fv[i] = 0;
+        if (i < npx) {
+            const u32 j = j0 + i;
+            if (t.fa >= 0) {
+                const int off = j < (u32)t.na ? t.fa + (int)j * d.elem : t.fb + (int)(j - (u32)t.na) * d.elem;
+                fv[i] = d.elem == 1 ? (u32)sb[off] : (u32)*reinterpret_cast<const u16 *>(sb + off);
+            } else {
+                const bool hyb = d.mode == MODE_HYBRID_EST;
+                const uint8_t *fsrc = hyb ? d.fbuf : d.src;
+                const long long fpitch = hyb ? d.f_pitch : d.src_pitch;
+                u32 y, x;
+                unit_pixel(d, t, j, y, x);
+                const uint8_t *fp = fsrc + (long long)y * fpitch + (long long)x * d.elem;
+                fv[i] = d.elem == 1 ? (u32)__ldcg(fp) : (u32)__ldcg(reinterpret_cast<const u16 *>(fp));
             }
         }
+    }
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const int j = j0 + r * kWarps;
-            if (j < g.th) {
-                const long long y = g.y0 + j;
-                float ya, yb = 0.f;
-                const u32 oa = wiener_ms(ma[r].x, ma[r].y, fa[r], k, ya);
-                const u32 ob = two ? wiener_ms(mb[r].x, mb[r].y, fb[r], k, yb) : 0u;
-                store_pair(d.dst + y * d.dst_pitch + (long long)(g.x0 + x) * d.elem, d.elem, two, oa, ob);
-                if (d.y_out) {
-                    float *yp = d.y_out + y * d.W + g.x0 + x;
-                    yp[0] = ya;
-                    if (two) yp[1] = yb;
-                }
+    for (int i = 0; i < 4; ++i) ov[i] = wiener_ms(mu[i], s2[i], fv[i], k, yv[i]);
+    u32 y, x;
+    unit_pixel(d, t, j0, y, x);
+    uint8_t *op = d.dst + (long long)y * d.dst_pitch + (long long)x * d.elem;
+    const uintptr_t oa = reinterpret_cast<uintptr_t>(op);
+    if (npx == 4 && same_row && d.elem == 1 && (oa & 3) == 0) {
+        *reinterpret_cast<u32 *>(op) = ov[0] | (ov[1] << 8) | (ov[2] << 16) | (ov[3] << 24);
+    } else if (npx == 4 && same_row && d.elem == 2 && (oa & 7) == 0) {
+        *reinterpret_cast<uint2 *>(op) = make_uint2(ov[0] | (ov[1] << 16), ov[2] | (ov[3] << 16));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < npx) {
+                u32 yy, xx;
+                unit_pixel(d, t, j0 + i, yy, xx);
+                uint8_t *o = d.dst + (long long)yy * d.dst_pitch + (long long)xx * d.elem;
+                if (d.elem == 1) *o = (uint8_t)ov[i];
+                else *reinterpret_cast<u16 *>(o) = (u16)ov[i];
             }
+        }
+    }
+    if (d.y_out) {
+        float *yp = d.y_out + q0 + j0;
+        if (npx == 4 && (reinterpret_cast<uintptr_t>(yp) & 15) == 0) {
+            *reinterpret_cast<float4 *>(yp) = make_float4(yv[0], yv[1], yv[2], yv[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i < npx) yp[i] = yv[i];
         }
     }
 }
@@ -1235,6 +1381,7 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
 
 // ---------------------------------------------------------------- one work item
 struct Views {
+    unsigned char *stage;     // plane-mode phase-2 stages (the whole dynamic area)
     u16 *fs, *gs, *wl0, *wl1;
     u32 *st_mm;
     u16 *st_c;
@@ -1307,23 +1454,6 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     HD_STAMP_INIT();
 
     const bool est = mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST;
-    if (phase == 2 && d.plane) {
-        // streaming apply from the plane: no f region needed
-        if (threadIdx.x == 0) {
-            if (bs.nu2_of != d.ctl) {
-                const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
-                bs.nu2 = nu2;
-                bs.nu2f = __double2float_rn(nu2);
-                bs.nu2_of = d.ctl;
-            }
-            if (g.x0 == 0 && g.y0 == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
-        }
-        __syncthreads();
-        if (mode == MODE_HYBRID_EST) tile_apply_plane(d, g, d.fbuf, d.f_pitch, bs.nu2f);
-        else tile_apply_plane(d, g, d.src, d.src_pitch, bs.nu2f);
-        HD_STAMP(6);
-        return;
-    }
 
     // ---- the f region in shared memory
     if (do_amf) {
@@ -1394,6 +1524,73 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     HD_STAMP(6);
 }
 
+// One phase-2 slot of a plane-mode image (all threads of the CTA): stream
+// units until the image has none left.
+__device__ __forceinline__ void p2_slot(const ImgDesc &d, int tile, const LaunchParams &lp, const Views &vw,
+                                     BlockShared &bs)
+{
+    const int U = (int)(((long long)d.H * d.W + kUnitPx - 1) / kUnitPx);
+    P2Claim cl;
+    if (threadIdx.x == 0) {
+        // generic writes to the stage area (earlier items) are ordered before
+        // the async copies into it; within the slot a stage is refilled only
+        // after the block barrier that ends its reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // first claim: the slot's share of the units (units / slots), at most
+        // a stage per unit, so that short images still spread over all slots
+        const int share = min(kStages, max(1, U / max(d.p2_items, 1)));
+        cl.blk = (int)atomicAdd(&d.ctl->p2_next, (u32)share);
+        cl.blk_left = share;
+        cl.spare = -1;
+        bool more = true;
+        for (int st = 0; st < kStages; ++st) {
+            const int u = more ? p2_next_unit(d, cl) : U;
+            more = u < U;
+            if (more) p2_issue(d, u, st, vw.stage, bs.st, bs.full);
+            else bs.st[st].unit = U;
+        }
+        if (bs.nu2_of != d.ctl) {
+            const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
+            bs.nu2 = nu2;
+            bs.nu2f = __double2float_rn(nu2);
+            bs.nu2_of = d.ctl;
+        }
+        if (tile == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
+    }
+    __syncthreads();
+    // stage k % kStages holds the k-th unit of the slot; units only grow, so
+    // the first empty stage ends the slot with no copy in flight
+    for (int k = 0;; ++k) {
+        const int st = k % kStages;
+        if (bs.st[st].unit >= U) break;
+        const bool late = !mbar_wait(&bs.full[st], (bs.fullpar >> st) & 1u, lp.spin_limit);
+        p2_apply(d, vw.stage + (size_t)st * kStageBytes, bs.st[st], bs.nu2f);
+        if (__syncthreads_or(late)) {
+            // a copy did not land in time: report, wait (bounded) for the
+            // slot's copies still in flight, and give up the slot
+            if (threadIdx.x == 0) {
+                atomicOr(&g_device_error, DEVERR_TIMEOUT);
+                for (int j = 0; j < kStages; ++j) {
+                    const int sj = (k + j) % kStages;
+                    if (bs.st[sj].unit < U) {
+                        mbar_wait(&bs.full[sj], (bs.fullpar >> sj) & 1u, lp.spin_limit);
+                        bs.fullpar ^= 1u << sj;
+                    }
+                    bs.st[sj].unit = U;
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        if (threadIdx.x == 0) {
+            bs.fullpar ^= 1u << st;
+            const int u = p2_next_unit(d, cl);
+            if (u < U) p2_issue(d, u, st, vw.stage, bs.st, bs.full);
+            else bs.st[st].unit = U;
+        }
+    }
+}
+
 __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
 {
     const long long n = (long long)d.w * d.w;
@@ -1403,6 +1600,20 @@ __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
 __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Views &vw,
                          BlockShared &bs, const int &next)
 {
+    if (phase == 2 && d.plane) {
+        // streaming apply from the plane: no tile geometry, no f region.  A
+        // CTA that has cached this image's noise variance has already seen its
+        // phase 1 complete and skips the wait.
+        HD_STAMP_INIT();
+        if (bs.nu2_of != d.ctl) {
+            const bool ok = wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag);
+            if (!ok) return;
+        }
+        HD_STAMP(7);
+        p2_slot(d, tile, lp, vw, bs);
+        HD_STAMP(6);
+        return;
+    }
     Geo g;
     g.Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1);
     int TW, TH;
@@ -1421,7 +1632,7 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
     g.gfx = g.x0 - g.Lm;
     g.gfy = g.y0 - g.Rw;
 
-    if (phase == 2) {
+    if (phase == 2 && bs.nu2_of != d.ctl) {
         HD_STAMP_INIT();
         const bool ok = wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag);
         HD_STAMP(7);
@@ -1440,6 +1651,7 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
     __shared__ BlockShared bs;
     const SmemLayout L = layout(lp.region_h, lp.ra_max, lp.wide);
     Views vw;
+    vw.stage = smem_raw;
     vw.fs = reinterpret_cast<u16 *>(smem_raw + L.fs);
     vw.gs = reinterpret_cast<u16 *>(smem_raw + L.gs);
     vw.wl0 = reinterpret_cast<u16 *>(smem_raw + L.wl);
@@ -1452,7 +1664,13 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
     const Seg *segs = lp.segs ? lp.segs : lp.oneseg;
     int buf = 0;
     int item;
-    if (threadIdx.x == 0) bs.nu2_of = nullptr;
+    if (threadIdx.x == 0) {
+        bs.nu2_of = nullptr;
+        bs.fullpar = 0;
+        for (int i = 0; i < kStages; ++i) mbar_init(&bs.full[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     if (lp.ticket) {
         if (threadIdx.x == 0) bs.item[0] = (int)atomicAdd(lp.ticket, 1u);
         __syncthreads();
@@ -1493,6 +1711,7 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
                 c.B_lo32 = 0;
                 c.B_hi32 = 0;
                 c.p1_done = 0;
+                c.p2_next = 0;
             }
             lp.ticket[0] = 0;
             lp.ticket[1] = 0;
