@@ -180,6 +180,8 @@ hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
  * so one image's Wiener overlaps another's median.  Each result is
  * bit-identical to the same image through hybrid_denoise (integer
  * reductions make the order irrelevant).
+ * A batch uses the recompute Wiener pass (no statistics plane): each image's
+ * Wiener tiles already run beside the next image's median tiles.
  * hybrid_denoise_batched writes the n descriptors into the workspace with
  * small kernels on `stream` (their bytes travel as kernel parameters), so the
  * call never waits for the device; the host array may be freed on return. */

@@ -263,15 +263,16 @@ BatchLayout batch_layout(const hd_image *imgs, int n)
     L.fbuf_off = off;
     L.fbuf_offsets.resize(n);
     L.plane_offsets.resize(n);
+    // a batch uses the recompute Wiener pass: an image's phase 2 already runs
+    // beside the next image's phase 1, and a statistics plane per image would
+    // add its traffic and slot overhead for no gain
     for (int i = 0; i < n; ++i) {
+        L.plane_offsets[i] = SIZE_MAX;
         if (hybrid_mode(&imgs[i]) == MODE_HYBRID_EST) {
             L.fbuf_offsets[i] = off;
             off += round_up((size_t)imgs[i].H * f_pitch_of(imgs[i].W, imgs[i].dtype), kAlign);
-            L.plane_offsets[i] = off;
-            off += plane_bytes(imgs[i].H, imgs[i].W);
         } else {
             L.fbuf_offsets[i] = SIZE_MAX;
-            L.plane_offsets[i] = SIZE_MAX;
         }
     }
     L.total = off;

@@ -57,6 +57,7 @@
 // slow on this part).
 #include <cuda_runtime.h>
 #include <climits>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include "hd_internal.h"
@@ -1757,15 +1758,26 @@ size_t smem_bytes(int region_h, int ra_max, int wide)
     return layout(region_h, ra_max, wide).total;
 }
 
+// The kernel's dynamic shared-memory limit only ever grows to the largest
+// size requested so far: launches and occupancy queries of smaller sizes stay
+// valid under it.
+static std::mutex g_attr_mu;
+static size_t g_attr_bytes = 48 * 1024;
+
+static cudaError_t ensure_smem_limit(size_t smem)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (smem <= g_attr_bytes) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(hd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) g_attr_bytes = smem;
+    return e;
+}
+
 int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *stream)
 {
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(hd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return (int)e;
-        configured = smem;
-    }
+    const cudaError_t e = ensure_smem_limit(smem);
+    if (e != cudaSuccess) return (int)e;
     hd_persistent_kernel<<<grid, kThreads, smem, (cudaStream_t)stream>>>(lp);
     return (int)cudaGetLastError();
 }
@@ -1773,16 +1785,14 @@ int launch_persistent(const LaunchParams &lp, int grid, size_t smem, void *strea
 int max_ctas_per_sm(size_t smem)
 {
     // occupancy per shared-memory size, cached (the query is not free)
+    static std::mutex mu;
     static size_t keys[16];
     static int vals[16];
     static int used = 0;
+    std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < used; ++i)
         if (keys[i] == smem) return vals[i];
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(hd_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return 0;
-    }
+    if (ensure_smem_limit(smem) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hd_persistent_kernel, kThreads, smem) != cudaSuccess)
         return 0;

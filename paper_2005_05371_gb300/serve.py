@@ -162,12 +162,11 @@ class Server:
         return int(r.host.numel() * r.host.element_size())
 
     def _request_bytes(self, r: Request) -> int:
-        # input + output + this image's share of a batched workspace (median plane,
-        # statistics plane of 8 bytes per pixel, tables)
+        # input + output + this image's share of a batched workspace (median plane, tables)
         b = self._img_bytes(r)
         H, W = r.host.shape
         es = r.host.element_size()
-        return 2 * ((b + ALIGN - 1) // ALIGN * ALIGN) + H * ((W * es + 15) // 16 * 16) + 8 * H * W + 3 * 1024
+        return 2 * ((b + ALIGN - 1) // ALIGN * ALIGN) + H * ((W * es + 15) // 16 * 16) + 3 * 1024
 
     def _admit(self):
         # keep room for the workspaces of the requests already admitted

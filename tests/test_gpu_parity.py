@@ -341,3 +341,19 @@ def test_wait_timeout_is_reported_and_recoverable():
     _, ref = oracle.hybrid(small, 5, 3)
     out, _, _ = gpu_hybrid(small, 5, 3)
     np.testing.assert_array_equal(out, ref.out32)
+
+
+def test_launches_with_varying_shared_memory():
+    """Launch sizes above 48 KB of shared memory in the order large, small,
+    middle, large: every launch must keep a valid dynamic shared-memory limit
+    (the limit only grows)."""
+    old = hd.hd_get_tuning()
+    try:
+        hd.hd_set_tuning(64, 0)
+        g = noisy_image(90, 150, np.uint16, seed=44)
+        for smax in (15, 11, 13, 15, 9, 15):
+            f, ref = oracle.hybrid(g, smax, 5, bits=12)
+            out, nu2, _ = gpu_hybrid(g, smax, 5, bits=12)
+            check_wiener(out, nu2, None, ref, 12)
+    finally:
+        hd.hd_set_tuning(*old)
