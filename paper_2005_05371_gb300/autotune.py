@@ -16,7 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE_PATH = os.path.join(HERE, "tuning.json")
-REGION_H = (16, 24, 32, 48, 64)
+REGION_H = (16, 24, 32, 40, 48, 56, 64)
 CTAS_PER_SM = (0, 2, 3)
 
 

@@ -902,7 +902,7 @@ struct P2Stage {
 };
 
 struct BlockShared {
-    int item[3];      // current / next ticket (double buffer), next ticket for the prefetch
+    int item[2];      // current / next ticket (double buffer)
     u64 full[kStages];        // plane-mode phase 2: stage s staged (bulk-copy bytes landed)
     P2Stage st[kStages];      //   what each stage holds
     u32 fullpar;              //   bit s: parity of the next phase to wait for on stage s
@@ -1037,8 +1037,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         split_add(&d.ctl->B_lo32, &d.ctl->B_hi32, sb);
         // release: the CTA's f tile and plane (ordered before this thread by
         // the barrier) and the sums become visible before the done count
-        __threadfence();
-        atomicAdd(&d.ctl->p1_done, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&d.ctl->p1_done) : "memory");
     }
 }
 
@@ -1093,11 +1092,6 @@ __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_gen
 __device__ __forceinline__ void mbar_init(u64 *m, u32 count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(u64 *m)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(m)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(u64 *m, u32 bytes)
@@ -1414,40 +1408,9 @@ __device__ __forceinline__ void tile_shape(int rw, int FH, int &Lm, int &TW, int
     TH = FH - 2 * rw;
 }
 
-// Warp 0 asks L2 for the noisy-input rows of the next median tile, so its
-// region load finds them on chip.  Only bytes inside image rows are touched.
-__device__ void prefetch_item(const LaunchParams &lp, int item)
-{
-    if (threadIdx.x >= 32 || item >= lp.total_items) return;
-    const Seg *segs = lp.segs ? lp.segs : lp.oneseg;
-    const Seg sg = segs[find_segment(segs, lp.nsegs, item)];
-    if (sg.phase != 1) return;
-    const ImgDesc &d = lp.descs ? lp.descs[sg.img] : lp.one;
-    if (!mode_median(d.mode)) return;
-    const int tile = item - sg.first;
-    const int Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1), Ra = d.smax >> 1;
-    int Lm, TW, TH;
-    tile_shape(Rw, lp.region_h, Lm, TW, TH);
-    const int tyi = tile / d.tiles_x, txi = tile - tyi * d.tiles_x;
-    const int x0 = txi * TW, y0 = tyi * TH;
-    const int tw = min(TW, d.W - x0), th = min(TH, d.H - y0);
-    const int gx0 = x0 - Lm - Ra - 1, gy0 = y0 - Rw - Ra;
-    const int rows = th + 2 * (Rw + Ra), cols = tw + Lm + Rw + 2 * Ra + 2;
-    const int xa = max(gx0, 0), xb = min(gx0 + cols, d.W);
-    for (int r = threadIdx.x; r < rows; r += 32) {
-        const uint8_t *rp = d.src + (long long)refl(gy0 + r, d.H) * d.src_pitch;
-        const uintptr_t a = reinterpret_cast<uintptr_t>(rp + (long long)xa * d.elem);
-        const uintptr_t b = reinterpret_cast<uintptr_t>(rp + (long long)xb * d.elem);
-        for (uintptr_t line = a & ~uintptr_t(127); line < b; line += 128) {
-            const uintptr_t p = line < a ? a : line;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
-    }
-}
-
 template <bool PACK, bool NARROW>
 __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const LaunchParams &lp, const Views &vw,
-                           BlockShared &bs, const int &next)
+                           BlockShared &bs)
 {
     const int mode = d.mode;
     const int FH = lp.region_h;
@@ -1462,11 +1425,8 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         load_region<false>(vw.gs + g.pa, g.GS, g.nrow + 2 * g.Ra, g.ncol + 2 * g.Ra, d.src, d.src_pitch, d.elem,
                            d.H, d.W, g.gfy - g.Ra, g.gfx - g.Ra, false,
                            d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem);
-        // the next ticket (taken when this item started) has arrived by now
-        if (lp.ticket && threadIdx.x == 0) bs.item[2] = next;
         __syncthreads();
         HD_STAMP(0);
-        if (lp.ticket) prefetch_item(lp, bs.item[2]);
         if (PACK) amf3_packed(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
         else amf3_scalar(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
         __syncthreads();
@@ -1599,7 +1559,7 @@ __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
 }
 
 __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Views &vw,
-                         BlockShared &bs, const int &next)
+                         BlockShared &bs)
 {
     if (phase == 2 && d.plane) {
         // streaming apply from the plane: no tile geometry, no f region.  A
@@ -1641,9 +1601,9 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
     }
     const bool pack = d.maxv < 0x8000;
     const bool narrow = image_narrow(d);
-    if (pack && narrow) run_item_t<true, true>(d, phase, g, lp, vw, bs, next);
-    else if (pack) run_item_t<true, false>(d, phase, g, lp, vw, bs, next);
-    else run_item_t<false, false>(d, phase, g, lp, vw, bs, next);
+    if (pack && narrow) run_item_t<true, true>(d, phase, g, lp, vw, bs);
+    else if (pack) run_item_t<true, false>(d, phase, g, lp, vw, bs);
+    else run_item_t<false, false>(d, phase, g, lp, vw, bs);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid_constant__ LaunchParams lp)
@@ -1688,7 +1648,7 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         // is always working on it: holding a later one cannot deadlock.
         int next = 0;
         if (lp.ticket && threadIdx.x == 0) next = (int)atomicAdd(lp.ticket, 1u);
-        run_item(d, sg.phase, item - sg.first, lp, vw, bs, next);
+        run_item(d, sg.phase, item - sg.first, lp, vw, bs);
         if (lp.ticket && threadIdx.x == 0) bs.item[buf ^ 1] = next;
         __syncthreads();
         if (lp.ticket) {
