@@ -141,7 +141,7 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     const int TW = (64 - lm - rw) & ~1, TH = t.region_h - 2 * rw;
     d.tiles_x = (img->W + TW - 1) / TW;
     d.tiles_y = (img->H + TH - 1) / TH;
-    d.p2_items = plane ? (int)(((long long)img->H * img->W + kUnitPx - 1) / kUnitPx) : d.tiles_x * d.tiles_y;
+    d.p2_items = plane ? 0 : d.tiles_x * d.tiles_y;
     return d;
 }
 
@@ -154,26 +154,6 @@ bool image_wide(const ImgDesc &d)
 }
 
 int halo_a(const ImgDesc &d) { return (d.mode == MODE_AMF || d.mode == MODE_HYBRID_EST || d.mode == MODE_HYBRID_GIVEN) ? d.smax / 2 : 0; }
-
-// Most CTAs a launch with this shape can keep resident (the persistent grid).
-int max_grid(const hd_tuning &t, int ra_max, int wide)
-{
-    const size_t smem = smem_bytes(t.region_h, ra_max, wide);
-    const int sms = device_sms();
-    int per_sm = max_ctas_per_sm(smem);
-    if (sms <= 0 || per_sm <= 0) return 0;
-    if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
-    return sms * per_sm;
-}
-
-// Phase-2 slots of a plane-mode image: two per resident CTA (a CTA holds up
-// to two tickets), at most one per chunk.
-void set_slots(ImgDesc &d, int grid)
-{
-    if (!d.plane) return;
-    const long long chunks = ((long long)d.H * d.W + kUnitPx - 1) / kUnitPx;
-    d.p2_items = (int)std::min<long long>(chunks, 2LL * std::max(grid, 1));
-}
 
 hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t *smem)
 {
@@ -189,7 +169,8 @@ hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t 
     int per_sm = max_ctas_per_sm(*smem);
     if (per_sm <= 0) return HD_ERR_CUDA;
     if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
-    *grid = std::max(1, std::min(lp.total_items, sms * per_sm));
+    // plane mode: every resident CTA takes a share of the phase-2 pixels
+    *grid = std::max(1, lp.p2_plane ? sms * per_sm : std::min(lp.total_items, sms * per_sm));
     return HD_OK;
 }
 
@@ -218,15 +199,18 @@ hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, c
     lp.descs = nullptr;
     lp.segs = nullptr;
     lp.one = make_desc(img, mode, t, ctl, fbuf, plane);
-    set_slots(lp.one, max_grid(t, halo_a(lp.one), image_wide(lp.one)));
     const int tiles = lp.one.tiles_x * lp.one.tiles_y;
     lp.oneseg[0] = Seg{0, 1, 0, tiles};
     lp.nsegs = 1;
     lp.total_items = tiles;
     if (two_phase) {
-        lp.oneseg[1] = Seg{0, 2, tiles, lp.one.p2_items};
-        lp.nsegs = 2;
-        lp.total_items = tiles + lp.one.p2_items;
+        if (plane) {
+            lp.p2_plane = 1;           // phase 2 runs after the queue, a share per CTA
+        } else {
+            lp.oneseg[1] = Seg{0, 2, tiles, lp.one.p2_items};
+            lp.nsegs = 2;
+            lp.total_items = tiles + lp.one.p2_items;
+        }
         lp.ticket = ticket;
         lp.ctl_reset = ctl;
         lp.nctl = 1;
@@ -310,8 +294,7 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
         bt.ra_max = std::max(bt.ra_max, halo_a(bt.descs[i]));
         bt.wide |= image_wide(bt.descs[i]) ? 1 : 0;
     }
-    const int grid = max_grid(t, bt.ra_max, bt.wide);
-    for (int i = 0; i < n; ++i) set_slots(bt.descs[i], grid);
+
     // ticket order: P1(0), P1(1), P2(0), P1(2), P2(1), ..., P2(n-1).  An image's
     // Wiener tiles follow its median tiles with one image of lag, so they seldom wait.
     long long first = 0;

@@ -35,8 +35,7 @@ struct ImgCtl {
     unsigned long long A_lo32, A_hi32;
     unsigned long long B_lo32, B_hi32;
     unsigned int p1_done;         // phase-1 tiles finished
-    unsigned int p2_next;         // next phase-2 unit of kUnitPx pixels (statistics-plane mode)
-    unsigned int pad[6];
+    unsigned int pad[7];
 };
 static_assert(sizeof(ImgCtl) == 64, "ImgCtl layout");
 
@@ -58,8 +57,7 @@ struct ImgDesc {
     int border_zero;          // Wiener border: 0 symmetric, 1 zero
     int mode;
     int tiles_x, tiles_y;
-    int p2_items;             // phase-2 work items: tiles, or with the plane, slots: a CTA holding a
-                              // slot applies units of kUnitPx pixels taken from ctl->p2_next
+    int p2_items;             // phase-2 queue items: the tiles (recompute pass), 0 with the plane
     float *plane;             // optional (estimated noise variance): per output pixel the
                               // binary32 pair (mu, s2) left by phase 1, row-major, W pairs a row;
                               // nullptr: phase 2 recomputes the sums from the f region
@@ -90,6 +88,8 @@ struct LaunchParams {
     int ra_max;               // largest median halo over the launch (shared memory sizing)
     int wide;                 // some image needs 64-bit Wiener sums
     unsigned long long spin_limit;   // bounded wait, in polls
+    int p2_plane;             // 1: `one` has a statistics plane; after the queue every CTA applies
+                              // its own 1/gridDim share of the image's pixels from it
 };
 
 // Shared-memory bytes the kernel needs.
@@ -120,9 +120,10 @@ size_t hybrid_control_bytes();
 size_t hybrid_min_bytes(const void *img);
 
 constexpr int kThreads = 256;
-// With the statistics plane, phase 2 streams units of kUnitPx consecutive
-// pixels in row-major order, staged in shared memory by bulk copies up to
-// kStages units ahead; every thread applies four pixels of a unit.
+// With the statistics plane, phase 2 streams each CTA's share of the pixels
+// (row-major order) in units of up to kUnitPx, staged in shared memory by
+// bulk copies up to kStages units ahead; every thread applies four pixels of
+// a unit.
 constexpr int kUnitPx = kThreads * 4;
 constexpr int kStages = 4;
 constexpr unsigned int DEVERR_TIMEOUT = 1u;

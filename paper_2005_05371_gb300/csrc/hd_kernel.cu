@@ -895,8 +895,9 @@ __device__ bool wait_phase1(const ImgDesc &d, u32 total, u64 limit, int *s_flag)
 }
 
 struct P2Stage {
-    int unit;         // staged unit, or the unit count when the stage is empty
-    int y0, x0;       // first pixel of the unit
+    u32 p0;           // first pixel of the unit (row-major index)
+    int n;            // its pixels (at most kUnitPx; 0: the stage is empty)
+    int y0, x0;       // row and column of p0
     int na;           // pixels of the unit in row y0
     int fa, fb;       // stage offsets of f for row y0 and row y0 + 1 (-1: f not staged)
 };
@@ -1082,11 +1083,13 @@ __device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const Apply
 }
 
 // ---------------------------------------------------------------- plane-mode phase 2
-// Units of kUnitPx pixels are staged in shared memory by bulk copies
-// (cp.async.bulk, completion counted on an mbarrier per stage) up to kStages
-// units ahead of the one being applied.  Thread 0 claims units from
-// ctl->p2_next and issues the copies; all threads apply; a block barrier per
-// unit frees its stage for the next copy.
+// Every CTA applies its own contiguous share of the image's pixels (all CTAs
+// reach phase 2 together, at the image-wide barrier, so equal shares are
+// balanced), in units of up to kUnitPx pixels staged in shared memory by bulk
+// copies (cp.async.bulk, completion counted on an mbarrier per stage) up to
+// kStages units ahead of the one being applied.  Thread 0 issues the copies;
+// all threads apply; a block barrier per unit frees its stage for the next
+// copy.
 __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(u64 *m, u32 count)
@@ -1129,14 +1132,12 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, u32 bytes,
                  : "memory");
 }
 
-// Thread 0: stage unit `unit` of image d into stage s.  Every address and
-// size is a multiple of 16 bytes and stays inside its buffer: the plane is
-// allocated in whole 256-byte blocks, f rows have a 16-byte-multiple pitch.
-__device__ void p2_issue(const ImgDesc &d, int unit, int s, unsigned char *stages, P2Stage *st, u64 *full)
+// Thread 0: stage pixels [q0, q0 + n) of image d (q0 even) into stage s.
+// Every address and size is a multiple of 16 bytes and stays inside its
+// buffer: the plane is allocated in whole 256-byte blocks, f rows have a
+// 16-byte-multiple pitch.
+__device__ void p2_issue(const ImgDesc &d, u32 q0, u32 n, int s, unsigned char *stages, P2Stage *st, u64 *full)
 {
-    const u32 HW = (u32)d.H * (u32)d.W;
-    const u32 q0 = (u32)unit * (u32)kUnitPx;
-    const u32 n = min((u32)kUnitPx, HW - q0);
     // row of q0: a binary32 estimate (off by at most one) corrected exactly
     const u32 W = (u32)d.W;
     u32 y0 = (u32)__fmul_rz((float)q0, __frcp_rz((float)W));
@@ -1147,7 +1148,8 @@ __device__ void p2_issue(const ImgDesc &d, int unit, int s, unsigned char *stage
     const u32 na = min(n, W - x0);
     unsigned char *sb = stages + (size_t)s * kStageBytes;
     P2Stage &t = st[s];
-    t.unit = unit;
+    t.p0 = q0;
+    t.n = (int)n;
     t.y0 = (int)y0;
     t.x0 = (int)x0;
     t.na = (int)na;
@@ -1172,23 +1174,6 @@ __device__ void p2_issue(const ImgDesc &d, int unit, int s, unsigned char *stage
     if (bbytes) bulk_copy(sb + kStagePlane + abytes, reinterpret_cast<const void *>(b0), bbytes, &full[s]);
 }
 
-// Unit claims of one slot (thread 0): a first block of the slot's share,
-// then one at a time, each claimed a unit ahead of its use.
-struct P2Claim {
-    int blk, blk_left, spare;
-};
-
-__device__ __forceinline__ int p2_next_unit(const ImgDesc &d, P2Claim &c)
-{
-    if (c.blk_left > 0) {
-        --c.blk_left;
-        return c.blk++;
-    }
-    const int u = c.spare >= 0 ? c.spare : (int)atomicAdd(&d.ctl->p2_next, 1u);
-    c.spare = (int)atomicAdd(&d.ctl->p2_next, 1u);
-    return u;
-}
-
 // Row and column of pixel j of a unit (j >= na: the following rows).
 __device__ __forceinline__ void unit_pixel(const ImgDesc &d, const P2Stage &t, u32 j, u32 &y, u32 &x)
 {
@@ -1210,9 +1195,7 @@ __device__ __forceinline__ void unit_pixel(const ImgDesc &d, const P2Stage &t, u
 // All threads: apply the staged unit (four pixels a thread).
 __device__ void p2_apply(const ImgDesc &d, const unsigned char *sb, const P2Stage &t, float v2f)
 {
-    const u32 HW = (u32)d.H * (u32)d.W;
-    const u32 q0 = (u32)t.unit * (u32)kUnitPx;
-    const u32 n = min((u32)kUnitPx, HW - q0);
+    const u32 q0 = t.p0, n = (u32)t.n;
     const u32 j0 = threadIdx.x * 4u;
     if (j0 >= n) return;
     const int npx = (int)min(4u, n - j0);
@@ -1487,57 +1470,50 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
 
 // One phase-2 slot of a plane-mode image (all threads of the CTA): stream
 // units until the image has none left.
-__device__ __forceinline__ void p2_slot(const ImgDesc &d, int tile, const LaunchParams &lp, const Views &vw,
-                                     BlockShared &bs)
+// Plane-mode phase 2 of the CTA's share of image d: pixels [pb, pe), the
+// gridDim.x shares being equal up to a pixel pair.
+__device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &vw, BlockShared &bs)
 {
-    const int U = (int)(((long long)d.H * d.W + kUnitPx - 1) / kUnitPx);
-    P2Claim cl;
+    if (!wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag)) return;
+    const u64 HW = (u64)d.H * (u64)d.W;
+    const u64 per = ((HW + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
+    const u32 pb = (u32)min(HW, 2 * per * blockIdx.x), pe = (u32)min(HW, 2 * per * (blockIdx.x + 1));
+    const int K = (int)((pe - pb + kUnitPx - 1) / kUnitPx);          // units of this share
     if (threadIdx.x == 0) {
-        // generic writes to the stage area (earlier items) are ordered before
-        // the async copies into it; within the slot a stage is refilled only
-        // after the block barrier that ends its reads
+        // generic writes to the stage area (phase-1 work) are ordered before
+        // the async copies into it; later a stage is refilled only after the
+        // block barrier that ends its reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        // first claim: the slot's share of the units (units / slots), at most
-        // a stage per unit, so that short images still spread over all slots
-        const int share = min(kStages, max(1, U / max(d.p2_items, 1)));
-        cl.blk = (int)atomicAdd(&d.ctl->p2_next, (u32)share);
-        cl.blk_left = share;
-        cl.spare = -1;
-        bool more = true;
         for (int st = 0; st < kStages; ++st) {
-            const int u = more ? p2_next_unit(d, cl) : U;
-            more = u < U;
-            if (more) p2_issue(d, u, st, vw.stage, bs.st, bs.full);
-            else bs.st[st].unit = U;
+            if (st < K) {
+                const u32 q = pb + (u32)st * kUnitPx;
+                p2_issue(d, q, min((u32)kUnitPx, pe - q), st, vw.stage, bs.st, bs.full);
+            } else {
+                bs.st[st].n = 0;
+            }
         }
-        if (bs.nu2_of != d.ctl) {
-            const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
-            bs.nu2 = nu2;
-            bs.nu2f = __double2float_rn(nu2);
-            bs.nu2_of = d.ctl;
-        }
-        if (tile == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
+        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
+        bs.nu2 = nu2;
+        bs.nu2f = __double2float_rn(nu2);
+        if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
     }
     __syncthreads();
-    // stage k % kStages holds the k-th unit of the slot; units only grow, so
-    // the first empty stage ends the slot with no copy in flight
-    for (int k = 0;; ++k) {
+    for (int k = 0; k < K; ++k) {
         const int st = k % kStages;
-        if (bs.st[st].unit >= U) break;
         const bool late = !mbar_wait(&bs.full[st], (bs.fullpar >> st) & 1u, lp.spin_limit);
         p2_apply(d, vw.stage + (size_t)st * kStageBytes, bs.st[st], bs.nu2f);
         if (__syncthreads_or(late)) {
             // a copy did not land in time: report, wait (bounded) for the
-            // slot's copies still in flight, and give up the slot
+            // copies still in flight, and give up the share
             if (threadIdx.x == 0) {
                 atomicOr(&g_device_error, DEVERR_TIMEOUT);
                 for (int j = 0; j < kStages; ++j) {
                     const int sj = (k + j) % kStages;
-                    if (bs.st[sj].unit < U) {
+                    if (bs.st[sj].n > 0) {
                         mbar_wait(&bs.full[sj], (bs.fullpar >> sj) & 1u, lp.spin_limit);
                         bs.fullpar ^= 1u << sj;
                     }
-                    bs.st[sj].unit = U;
+                    bs.st[sj].n = 0;
                 }
             }
             __syncthreads();
@@ -1545,9 +1521,13 @@ __device__ __forceinline__ void p2_slot(const ImgDesc &d, int tile, const Launch
         }
         if (threadIdx.x == 0) {
             bs.fullpar ^= 1u << st;
-            const int u = p2_next_unit(d, cl);
-            if (u < U) p2_issue(d, u, st, vw.stage, bs.st, bs.full);
-            else bs.st[st].unit = U;
+            const int kn = k + kStages;
+            if (kn < K) {
+                const u32 q = pb + (u32)kn * kUnitPx;
+                p2_issue(d, q, min((u32)kUnitPx, pe - q), st, vw.stage, bs.st, bs.full);
+            } else {
+                bs.st[st].n = 0;
+            }
         }
     }
 }
@@ -1561,20 +1541,6 @@ __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
 __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Views &vw,
                          BlockShared &bs)
 {
-    if (phase == 2 && d.plane) {
-        // streaming apply from the plane: no tile geometry, no f region.  A
-        // CTA that has cached this image's noise variance has already seen its
-        // phase 1 complete and skips the wait.
-        HD_STAMP_INIT();
-        if (bs.nu2_of != d.ctl) {
-            const bool ok = wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag);
-            if (!ok) return;
-        }
-        HD_STAMP(7);
-        p2_slot(d, tile, lp, vw, bs);
-        HD_STAMP(6);
-        return;
-    }
     Geo g;
     g.Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1);
     int TW, TH;
@@ -1658,6 +1624,8 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
             item += gridDim.x;
         }
     }
+    // plane mode: every CTA applies its share of the image's phase 2
+    if (lp.p2_plane) p2_share(lp.one, lp, vw, bs);
     // The last CTA out leaves the queue counters and control blocks zeroed
     // for the next launch on this workspace.
     if (lp.ticket && threadIdx.x == 0) {
@@ -1672,7 +1640,6 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
                 c.B_lo32 = 0;
                 c.B_hi32 = 0;
                 c.p1_done = 0;
-                c.p2_next = 0;
             }
             lp.ticket[0] = 0;
             lp.ticket[1] = 0;
