@@ -920,7 +920,8 @@ struct BlockShared {
 // ---------------------------------------------------------------- Wiener passes
 struct ApplyConst {
     u32 n;
-    float v2f, inv_n, inv_n2, maxv;
+    float v2f, inv_n, inv_n2;
+    u32 maxv;
 };
 
 // Phase-1 statistics of one tile: sum over its pixels of S1^2 (A) and of
@@ -1058,9 +1059,9 @@ __device__ __forceinline__ u32 wiener_px(u32 s1, float dfl, u32 fv, const ApplyC
     } else {
         y = mu;
     }
-    float q = floorf(__fadd_rn(y, 0.5f));
-    q = fminf(fmaxf(q, 0.0f), k.maxv);
-    return (u32)q;
+    // floor(y + 0.5) clamped to [0, maxv]: the round-down conversion saturates
+    // negatives (and NaN) to 0
+    return min(__float2uint_rd(__fadd_rn(y, 0.5f)), k.maxv);
 }
 
 // binary32 Wiener output from the stored (mu, s2) of a pixel.
@@ -1077,9 +1078,9 @@ __device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const Apply
     } else {
         y = mu;
     }
-    float q = floorf(__fadd_rn(y, 0.5f));
-    q = fminf(fmaxf(q, 0.0f), k.maxv);
-    return (u32)q;
+    // floor(y + 0.5) clamped to [0, maxv]: the round-down conversion saturates
+    // negatives (and NaN) to 0
+    return min(__float2uint_rd(__fadd_rn(y, 0.5f)), k.maxv);
 }
 
 // ---------------------------------------------------------------- plane-mode phase 2
@@ -1204,7 +1205,7 @@ __device__ void p2_apply(const ImgDesc &d, const unsigned char *sb, const P2Stag
     k.v2f = v2f;
     k.inv_n = 0.f;
     k.inv_n2 = 0.f;
-    k.maxv = (float)d.maxv;
+    k.maxv = (u32)d.maxv;
     const float4 *pp = reinterpret_cast<const float4 *>(sb) + 2 * threadIdx.x;
     const float4 m01 = pp[0], m23 = pp[1];
     const float mu[4] = {m01.x, m01.z, m23.x, m23.z};
@@ -1278,7 +1279,7 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     k.v2f = v2f;
     k.inv_n = __frcp_rn((float)k.n);
     k.inv_n2 = __frcp_rn((float)(k.n * k.n));
-    k.maxv = (float)d.maxv;
+    k.maxv = (u32)d.maxv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = 2 * lane;
     const int per = (g.th + kWarps - 1) / kWarps;
