@@ -58,6 +58,7 @@
 #include <cuda_runtime.h>
 #include <climits>
 #include <mutex>
+#include <type_traits>
 #include <cstdint>
 #include <cstring>
 #include "hd_internal.h"
@@ -777,12 +778,14 @@ __device__ void hsums(const Geo &g, const u16 *fs, u32 *H1, void *h2p, int w, bo
         const int xs = 8 * m, xe = min(xs + 8, g.tw);
         const u16 *fr = fs + j * FS + g.hx;
         u32 *h1 = H1 + j * HS;
+        // NARROW: the window sums of f^2 are exact in 32 bits
+        using S2 = typename std::conditional<NARROW, u32, u64>::type;
         u32 s1 = 0;
-        u64 s2 = 0;
+        S2 s2 = 0;
         for (int t = 0; t < w; ++t) {
             const u32 f = fr[xs + t];
             s1 += f;
-            if (with_h2) s2 += (u64)(f * f);
+            if (with_h2) s2 += (S2)(f * f);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -791,14 +794,14 @@ __device__ void hsums(const Geo &g, const u16 *fs, u32 *H1, void *h2p, int w, bo
                 h1[x] = s1;
                 if (with_h2) {
                     if (NARROW) reinterpret_cast<u32 *>(h2p)[j * HS + x] = (u32)s2;
-                    else reinterpret_cast<u64 *>(h2p)[j * HS + x] = s2;
+                    else reinterpret_cast<u64 *>(h2p)[j * HS + x] = (u64)s2;
                 }
                 if (x + 1 < xe) {
                     const u32 a = fr[x + w], b = fr[x];
                     s1 += a - b;
                     if (with_h2) {
-                        s2 += (u64)(a * a);
-                        s2 -= (u64)(b * b);
+                        s2 += (S2)(a * a);
+                        s2 -= (S2)(b * b);
                     }
                 }
             }
@@ -972,6 +975,9 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
                 }
             }
         }
+        float2 *pp = with_plane ? reinterpret_cast<float2 *>(d.plane) + (long long)(g.y0 + j0) * d.W + g.x0 + x
+                                : nullptr;
+        const bool pair16 = two && ((d.W | g.x0) & 1) == 0;      // (mu, s2) pairs land 16-byte aligned
         for (int j = j0; j < j1; ++j) {
             const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
             const u32 fa = fp & 0xffffu, fb = fp >> 16;
@@ -996,9 +1002,15 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
                     da = __ull2float_rn((u64)n * wa - (u64)sa * sa);
                     db = __ull2float_rn((u64)n * wb - (u64)sb * sb);
                 }
-                float2 *pp = reinterpret_cast<float2 *>(d.plane) + (long long)(g.y0 + j) * d.W + g.x0 + x;
-                pp[0] = make_float2(__fmul_rn(__uint2float_rn(sa), inv_n), __fmul_rn(da, inv_n2));
-                if (two) pp[1] = make_float2(__fmul_rn(__uint2float_rn(sb), inv_n), __fmul_rn(db, inv_n2));
+                const float mua = __fmul_rn(__uint2float_rn(sa), inv_n), s2a = __fmul_rn(da, inv_n2);
+                const float mub = __fmul_rn(__uint2float_rn(sb), inv_n), s2b = __fmul_rn(db, inv_n2);
+                if (pair16) {
+                    *reinterpret_cast<float4 *>(pp) = make_float4(mua, s2a, mub, s2b);
+                } else {
+                    pp[0] = make_float2(mua, s2a);
+                    if (two) pp[1] = make_float2(mub, s2b);
+                }
+                pp += d.W;
             }
             if (j + 1 < j1) {
                 const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
