@@ -1491,20 +1491,27 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
     const u64 HW = (u64)d.H * (u64)d.W;
     const u64 per = ((HW + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
     const u32 pb = (u32)min(HW, 2 * per * blockIdx.x), pe = (u32)min(HW, 2 * per * (blockIdx.x + 1));
-    const int K = (int)((pe - pb + kUnitPx - 1) / kUnitPx);          // units of this share
-    if (threadIdx.x == 0) {
+    // K units of one even size (the last one takes the remainder): every unit
+    // starts inside the share
+    const u32 S = pe - pb, K0 = (S + kUnitPx - 1) / kUnitPx;
+    const u32 usz = K0 > 0 ? min((u32)kUnitPx, ((S + K0 - 1) / K0 + 1) & ~1u) : 1u;
+    const int K = (int)((S + usz - 1) / usz);
+    // priming: lanes 0..kStages-1 of warp 0 stage one unit each; a thread of
+    // warp 1 converts the noise variance meanwhile
+    if (threadIdx.x < kStages) {
+        const int st = threadIdx.x;
         // generic writes to the stage area (phase-1 work) are ordered before
         // the async copies into it; later a stage is refilled only after the
         // block barrier that ends its reads
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int st = 0; st < kStages; ++st) {
-            if (st < K) {
-                const u32 q = pb + (u32)st * kUnitPx;
-                p2_issue(d, q, min((u32)kUnitPx, pe - q), st, vw.stage, bs.st, bs.full);
-            } else {
-                bs.st[st].n = 0;
-            }
+        if (st < K) {
+            const u32 q = pb + (u32)st * usz;
+            p2_issue(d, q, min(usz, pe - q), st, vw.stage, bs.st, bs.full);
+        } else {
+            bs.st[st].n = 0;
         }
+    }
+    if (threadIdx.x == 32) {
         const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
         bs.nu2 = nu2;
         bs.nu2f = __double2float_rn(nu2);
@@ -1536,8 +1543,8 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
             bs.fullpar ^= 1u << st;
             const int kn = k + kStages;
             if (kn < K) {
-                const u32 q = pb + (u32)kn * kUnitPx;
-                p2_issue(d, q, min((u32)kUnitPx, pe - q), st, vw.stage, bs.st, bs.full);
+                const u32 q = pb + (u32)kn * usz;
+                p2_issue(d, q, min(usz, pe - q), st, vw.stage, bs.st, bs.full);
             } else {
                 bs.st[st].n = 0;
             }
