@@ -715,10 +715,112 @@ __device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *se
     }
 }
 
+// The exact median of the K x K window at ctr, known to lie strictly between
+// zmin and zmax, by one thread: the same value-snapping bisection as the
+// cooperative selection, over the whole window.
+template <int K>
+__device__ u32 median_snap(const u16 *ctr, int GS, u32 zmin, u32 zmax)
+{
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    u32 lo = zmin + 1, hi = zmax - 1;
+    while (lo < hi) {
+        const u32 t = (lo + hi) >> 1;
+        u32 c = 0, below = 0, above = 0xffffu;
+#pragma unroll 1
+        for (int dy = -R; dy <= R; ++dy) {
+            const u16 *row = ctr + dy * GS;
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                const u32 v = row[dx];
+                const bool le = v <= t;
+                c += le;
+                below = umax(below, le ? v : 0u);
+                above = umin(above, le ? 0xffffu : v);
+            }
+        }
+        if (c > (u32)M0) hi = below;
+        else lo = above;
+    }
+    return lo;
+}
+
+// Levels A and B of one pixel for the K x K window (whole-window extremes and
+// counts); returns true with the output in `out` when the pixel is resolved.
+template <int K>
+__device__ __forceinline__ bool level_one(const u16 *ctr, int GS, u32 zxy, bool last, bool keep, u32 &out)
+{
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    u32 zmin = 0xffffu, zmax = 0u, cmin = 0, cmax = 0;
+#pragma unroll 1
+    for (int dy = -R; dy <= R; ++dy) {
+        const u16 *row = ctr + dy * GS;
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) {
+            const u32 v = row[dx];
+            zmin = umin(zmin, v);
+            zmax = umax(zmax, v);
+        }
+    }
+#pragma unroll 1
+    for (int dy = -R; dy <= R; ++dy) {
+        const u16 *row = ctr + dy * GS;
+#pragma unroll
+        for (int dx = -R; dx <= R; ++dx) {
+            const u32 v = row[dx];
+            cmin += v == zmin;
+            cmax += v == zmax;
+        }
+    }
+    if (cmin <= (u32)M0 && cmax <= (u32)M0) {
+        if (zmin < zxy && zxy < zmax) out = zxy;
+        else out = K == 5 ? median25(ctr, GS) : median_snap<K>(ctr, GS, zmin, zmax);
+        return true;
+    }
+    if (last) {
+        out = keep ? zxy : (cmin > (u32)M0 ? zmin : zmax);
+        return true;
+    }
+    return false;
+}
+
+// Warp 0, when at most 32 pixels failed level A at 3x3: one pixel per lane
+// through the windows k = 5..Smax, with no block barriers (the worklist path
+// pays two or three per window size for a handful of pixels).
+__device__ void grow_small(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, const u16 *list, int n)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane >= n) return;
+    const u32 ent = list[lane];
+    const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+    const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
+    const u32 zxy = ctr[0];
+    const bool keep = d.unresolved != 0;
+    u32 out = zxy;
+    for (int k = 5; k <= d.smax; k += 2) {
+        const bool last = k == d.smax;
+        bool done;
+        switch (k) {
+        case 5: done = level_one<5>(ctr, g.GS, zxy, last, keep, out); break;
+        case 7: done = level_one<7>(ctr, g.GS, zxy, last, keep, out); break;
+        case 9: done = level_one<9>(ctr, g.GS, zxy, last, keep, out); break;
+        case 11: done = level_one<11>(ctr, g.GS, zxy, last, keep, out); break;
+        case 13: done = level_one<13>(ctr, g.GS, zxy, last, keep, out); break;
+        default: done = level_one<15>(ctr, g.GS, zxy, last, keep, out); break;
+        }
+        if (done) break;
+    }
+    fs[r * FS + c] = (u16)out;
+}
+
 // Windows k = 5..Smax for the pixels that failed level A at k = 3.
 __device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl0, u16 *wl1, int *cnt,
                          int cap, u32 *st_mm, u16 *st_c)
 {
+    const int n0 = cnt[0];
+    if (n0 <= 32) {
+        if (n0 > 0 && threadIdx.x < 32) grow_small(d, g, gs, fs, wl0, n0);
+        return;
+    }
     const bool keep = d.unresolved != 0;
     u16 *cur = wl0, *nxt = wl1;
     int ci = 0;
@@ -1429,7 +1531,9 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         HD_STAMP(1);
         if (d.smax > 3) amf_grow(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW, vw.st_mm, vw.st_c);
         if (g.Rw > 0 && d.border_zero) {
-            // zero-border Wiener: samples outside the image read 0
+            // zero-border Wiener: samples outside the image read 0 (after every
+            // growth write: the short-worklist path ends without a barrier)
+            __syncthreads();
             for (int i = threadIdx.x; i < g.nrow * g.ncol; i += kThreads) {
                 const int r = i / g.ncol, c = i - r * g.ncol;
                 const int gy = g.gfy + r, gx = g.gfx + c;
