@@ -310,6 +310,17 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
     const bool zrows = zero_outside && (gy0 < 0 || gy0 + rows > H);
     if (left || right || zrows) {
         __syncthreads();
+        if (!zero_outside) {
+            // reflection: only the halo columns are written
+            const int nl = left ? -gx0 : 0, nr = right ? gx0 + cols - W : 0, nh = nl + nr;
+            for (int i = threadIdx.x; i < rows * nh; i += kThreads) {
+                const int r = i / nh, k = i - r * nh;
+                const int c = k < nl ? k : cols - nr + (k - nl);
+                const int sc = refl(gx0 + c, W) - gx0;
+                dst[r * ds + c] = (sc >= 0 && sc < cols) ? dst[r * ds + sc] : (u16)0;
+            }
+            return;
+        }
         for (int i = threadIdx.x; i < rows * cols; i += kThreads) {
             const int r = i / cols, c = i - r * cols;
             const int gx = gx0 + c, gy = gy0 + r;
