@@ -123,6 +123,11 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     d.dst_pitch = (long long)img->dst_pitch;
     d.f_pitch = (long long)f_pitch_of(img->W, img->dtype);
     d.noise_var = img->p.noise_var;
+    {
+        // the host's IEEE division gives the correctly rounded reciprocal
+        const double nw = (double)img->p.wiener_w * (double)img->p.wiener_w;
+        d.inv_den = 1.0 / (nw * nw * (double)img->H * (double)img->W);
+    }
     d.noise_var_out = img->noise_var_out;
     d.y_out = img->y_out;
     d.ctl = ctl;

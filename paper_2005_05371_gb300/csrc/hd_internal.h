@@ -44,7 +44,8 @@ struct ImgDesc {
     uint8_t *dst;
     uint8_t *fbuf;            // median output plane (MODE_HYBRID_EST)
     long long src_pitch, dst_pitch, f_pitch;   // bytes
-    double noise_var;         // < 0: estimate
+    double noise_var;
+    double inv_den;           // RN(1 / (n^2 H W)), for the correctly rounded noise-variance quotient         // < 0: estimate
     double *noise_var_out;    // optional
     float *y_out;             // optional, pitch W floats
     ImgCtl *ctl;

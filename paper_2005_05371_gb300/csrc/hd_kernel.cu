@@ -972,11 +972,17 @@ __device__ double u128_to_double(u64 hi, u64 lo)
     u64 top = s == 0 ? hi : ((hi << s) | (lo >> (64 - s)));
     const u64 rest = lo << s;
     top |= (rest != 0ull) ? 1ull : 0ull;    // sticky bit, far below the rounding position
-    return scalbn(__ull2double_rn(top), 64 - s);
+    // exact scaling by 2^(64 - s) (1 <= 64 - s <= 64: a normal power of two)
+    return __ull2double_rn(top) * __longlong_as_double((long long)(1023 + 64 - s) << 52);
 }
 
-// nu2 = fl(fl(n * B - A) / (n^2 H W)) from the two exact per-image sums.
-__device__ double noise_variance(const ImgCtl *ctl, u64 n, int H, int W)
+// nu2 = fl(fl(n * B - A) / (n^2 H W)) from the two exact per-image sums.  The
+// quotient a / b uses the reciprocal y = RN(1 / b) from the host and
+// Markstein's correction (P. Markstein, IBM J. Res. Dev. 34(1), 1990): with
+// q0 = RN(a y) (within an ulp of a / b) and the exact remainder r = a - b q0
+// (one fused multiply-add), RN(q0 + r y) = RN(a / b).  b = n^2 H W < 2^53 is
+// exact; a is far from overflow and underflow.
+__device__ double noise_variance(const ImgCtl *ctl, u64 n, int H, int W, double inv_den)
 {
     u64 alo, ahi, blo, bhi;
     split_total(__ldcg(&ctl->A_lo32), __ldcg(&ctl->A_hi32), ahi, alo);
@@ -986,7 +992,10 @@ __device__ double noise_variance(const ImgCtl *ctl, u64 n, int H, int W)
     const u64 dlo = nlo - alo;
     const u64 dhi = nhi - ahi - (nlo < alo ? 1ull : 0ull);
     const double denom = (double)n * (double)n * (double)H * (double)W;
-    return __ddiv_rn(u128_to_double(dhi, dlo), denom);
+    const double a = u128_to_double(dhi, dlo);
+    const double q0 = __dmul_rn(a, inv_den);
+    const double r = __fma_rn(-denom, q0, a);
+    return __fma_rn(r, inv_den, q0);
 }
 
 __device__ bool wait_phase1(const ImgDesc &d, u32 total, u64 limit, int *s_flag)
@@ -1584,7 +1593,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     if (threadIdx.x == 0) {
         if (!est || bs.nu2_of != d.ctl) {
             const u64 n = (u64)d.w * (u64)d.w;
-            const double nu2 = est ? noise_variance(d.ctl, n, d.H, d.W) : d.noise_var;
+            const double nu2 = est ? noise_variance(d.ctl, n, d.H, d.W, d.inv_den) : d.noise_var;
             bs.nu2 = nu2;
             bs.nu2f = __double2float_rn(nu2);
             bs.nu2_of = est ? d.ctl : nullptr;
@@ -1603,6 +1612,9 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
 __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &vw, BlockShared &bs)
 {
     if (!wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag)) return;
+    // the plane and f rows were written by other CTAs (generic stores, made
+    // visible by the wait); the bulk copies read them through the async proxy
+    if (threadIdx.x < kStages) asm volatile("fence.proxy.async.global;" ::: "memory");
     const u64 HW = (u64)d.H * (u64)d.W;
     const u64 per = ((HW + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
     const u32 pb = (u32)min(HW, 2 * per * blockIdx.x), pe = (u32)min(HW, 2 * per * (blockIdx.x + 1));
@@ -1627,7 +1639,7 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
         }
     }
     if (threadIdx.x == 32) {
-        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W);
+        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W, d.inv_den);
         bs.nu2 = nu2;
         bs.nu2f = __double2float_rn(nu2);
         if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
