@@ -145,6 +145,8 @@ hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p,
  * (pinned memory gives overlap-free full-speed copies; pageable works).  The
  * call copies src into the workspace, runs hybrid_denoise there, copies the
  * result back to dst and waits for the stream.  Returns after dst is written.
+ * A host buffer whose pitch equals W * element size moves as one linear copy;
+ * a padded one moves row by row (slower for many short rows).
  * workspace: device, >= hybrid_host_workspace_size() bytes. */
 hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_bytes,
                               hd_stream_t stream);

@@ -428,7 +428,7 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
     size_t b = 0;
     hd_status st = hybrid_workspace_size(H, W, dtype, p, &b);
     if (st != HD_OK) return st;
-    const size_t plane = round_up((size_t)H * f_pitch_of(W, dtype), kAlign);
+    const size_t plane = round_up((size_t)H * (size_t)W * elem_size(dtype), kAlign);
     *bytes = round_up(b, kAlign) + 2 * plane;
     return HD_OK;
 }
@@ -444,16 +444,20 @@ hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_by
     size_t core = 0;
     hybrid_workspace_size(img->H, img->W, img->dtype, &img->p, &core);
     core = round_up(core, kAlign);
-    const size_t pitch = f_pitch_of(img->W, img->dtype);
+    // device planes at the tight row pitch: a tight host buffer then moves as
+    // one linear copy each way (a pitched copy moves row by row)
+    const size_t row = (size_t)img->W * elem_size(img->dtype);
+    const size_t pitch = row;
     const size_t plane = round_up((size_t)img->H * pitch, kAlign);
     uint8_t *base = static_cast<uint8_t *>(workspace);
     uint8_t *dsrc = base + core;
     uint8_t *ddst = dsrc + plane;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t row = (size_t)img->W * elem_size(img->dtype);
-    if (cudaMemcpy2DAsync(dsrc, pitch, img->src, img->src_pitch, row, img->H, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return HD_ERR_CUDA;
+    const cudaError_t ein = img->src_pitch == row
+                                ? cudaMemcpyAsync(dsrc, img->src, row * img->H, cudaMemcpyHostToDevice, s)
+                                : cudaMemcpy2DAsync(dsrc, pitch, img->src, img->src_pitch, row, img->H,
+                                                    cudaMemcpyHostToDevice, s);
+    if (ein != cudaSuccess) return HD_ERR_CUDA;
     hd_image dimg = *img;
     dimg.src = dsrc;
     dimg.dst = ddst;
@@ -461,9 +465,11 @@ hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_by
     dimg.dst_pitch = pitch;
     st = run_single(&dimg, hybrid_mode(&dimg), core ? workspace : nullptr, core, s);
     if (st != HD_OK) return st;
-    if (cudaMemcpy2DAsync(img->dst, img->dst_pitch, ddst, pitch, row, img->H, cudaMemcpyDeviceToHost, s) !=
-        cudaSuccess)
-        return HD_ERR_CUDA;
+    const cudaError_t eout = img->dst_pitch == row
+                                 ? cudaMemcpyAsync(img->dst, ddst, row * img->H, cudaMemcpyDeviceToHost, s)
+                                 : cudaMemcpy2DAsync(img->dst, img->dst_pitch, ddst, pitch, row, img->H,
+                                                     cudaMemcpyDeviceToHost, s);
+    if (eout != cudaSuccess) return HD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return HD_ERR_CUDA;
     return HD_OK;
 }

@@ -272,6 +272,23 @@ def test_hybrid_host_buffers():
     np.testing.assert_array_equal(out16, ref16.out32)
 
 
+def test_hybrid_host_buffers_with_row_padding():
+    """Host rows wider than the image (views into padded arrays): the copies
+    move row by row instead of as one block; tight and padded buffers mixed."""
+    for dtype, bits, (H, W) in ((np.uint8, 8, (61, 93)), (np.uint16, 12, (45, 70))):
+        g = noisy_image(H, W, dtype, seed=9)
+        _, ref = oracle.hybrid(g, 9, 5, bits=bits)
+        gp = np.zeros((H, W + 13), dtype)
+        gp[:, :W] = g
+        for src in (g, gp[:, :W]):
+            for pad in (0, 7):
+                big = np.full((H, W + pad), 5, dtype)
+                out = big[:, :W]
+                hd.hybrid_denoise_host(src, out, smax=9, wiener_w=5, bits=bits)
+                np.testing.assert_array_equal(out, ref.out32)
+                assert (big[:, W:] == 5).all()
+
+
 # ------------------------------------------------------------------ batches
 def _batch_items(n, seed):
     rng = np.random.default_rng(seed)
