@@ -14,7 +14,10 @@ What each function follows in the paper:
                      form (local mean / variance over w x w, noise variance =
                      mean local variance unless supplied).
 * ``hybrid``       - Algorithm 1, step 4: Wiener(AMF(g)).  The contrast
-                     stretch of step 4e is not part of this path.
+                     stretch of step 4e is the separate ``contrast``.
+* ``contrast``     - Algorithm 1, step 4e (the paper gives no rule): linear
+                     stretch between the k-th smallest and k-th largest
+                     values, k = floor(tol * N), exact integer rounding.
 
 Pins: every function here is checked, in ``tests/test_oracle_pins.py``,
 against brute force on tiny images, library order-statistic filters,
@@ -71,6 +74,8 @@ def _load():
             lib.oracle_wiener_stats.restype = I
             lib.oracle_amf_pixel.argtypes = [P, L, L, I, I, L, L]
             lib.oracle_amf_pixel.restype = I
+            lib.oracle_contrast.argtypes = [P, L, I, ctypes.c_double, P, P]
+            lib.oracle_contrast.restype = I
             lib.oracle_check_smax.argtypes = [I]
             lib.oracle_check_smax.restype = I
             _lib = lib
@@ -188,3 +193,22 @@ def hybrid(g: np.ndarray, smax: int, w: int, noise_var: float = -1.0, bits: int 
     """
     f = amf(g, smax, keep_unresolved=keep_unresolved)
     return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero)
+
+
+def contrast(x: np.ndarray, tol: float = 0.01, bits: int | None = None):
+    """Contrast stretch of an integer image (Algorithm 1, step 4e, read as a
+    linear stretch between saturation limits; see ``oracle_contrast``).
+
+    Returns ``(out, lo, hi)``: the stretched image with ``x``'s dtype and the
+    two limits.  ``bits`` sets maxv = 2^bits - 1 (default 8 for uint8, 16 for
+    uint16)."""
+    lib = _load()
+    x16 = _as_u16(x)
+    if bits is None:
+        bits = 8 if x.dtype == np.uint8 else 16
+    out = np.empty_like(x16)
+    lohi = np.zeros(2, dtype=np.int64)
+    rc = lib.oracle_contrast(_ptr(x16), x16.size, int(bits), float(tol), _ptr(out), _ptr(lohi))
+    if rc != ORACLE_OK:
+        raise OracleError(rc, "oracle_contrast")
+    return out.astype(x.dtype), int(lohi[0]), int(lohi[1])

@@ -33,6 +33,9 @@
  * uses for its FP32 gain, so that the integer rounding decision can be
  * compared in the same precision on both sides.
  *
+ * Contrast stretch (Algorithm 1, step 4e; a separate post-step, see
+ * oracle_contrast): linear between histogram saturation limits.
+ *
  * Borders: out-of-range indices map by half-sample symmetric reflection with
  * period 2N (the paper states no border rule), or, for the Wiener stage only,
  * read as zero while still counting in n.
@@ -300,4 +303,58 @@ int oracle_amf_pixel(const uint16_t *g, long H, long W, int Smax, int keep_unres
     }
     free(win);
     return result;
+}
+
+/*
+ * Contrast stretch (Algorithm 1, step 4e; the post-processing box of the
+ * hybrid's architecture figure).  The paper names the step and gives no rule.
+ * Reading: a linear stretch between two saturation limits taken from the
+ * image's histogram, so that at most k pixels saturate at each end,
+ *   k  = floor(fl64(tol * N)),  0 <= tol < 1/2,  N = number of pixels,
+ *   lo = the smallest v with #{x <= v} >= k + 1   (the k-th smallest value, from 0),
+ *   hi = the smallest v with #{x <= v} >= N - k   (the k-th largest value),
+ *   lo == hi:  out = x                            (nothing to stretch),
+ *   otherwise  out = floor((clamp(x, lo, hi) - lo) * maxv / (hi - lo) + 1/2)
+ * with exact integers (round half up).  tol = 0 is the min-max stretch.
+ * lohi (optional) receives lo and hi.
+ */
+int oracle_contrast(const uint16_t *x, long N, int bits, double tol, uint16_t *out, long *lohi)
+{
+    if (!x || !out || N < 1 || bits < 1 || bits > 16) return ORACLE_ERR_ARG;
+    if (!(tol >= 0.0 && tol < 0.5)) return ORACLE_ERR_ARG;
+    const long maxv = (1L << bits) - 1;
+    uint64_t *hist = (uint64_t *)calloc((size_t)maxv + 1, sizeof(uint64_t));
+    if (!hist) return ORACLE_ERR_OOM;
+    for (long i = 0; i < N; ++i) {
+        if (x[i] > maxv) {
+            free(hist);
+            return ORACLE_ERR_ARG;
+        }
+        hist[x[i]] += 1;
+    }
+    const uint64_t k = (uint64_t)floor(tol * (double)N);
+    const uint64_t t_lo = k + 1, t_hi = (uint64_t)N - k;
+    long lo = -1, hi = -1;
+    uint64_t cum = 0;
+    for (long v = 0; v <= maxv; ++v) {
+        cum += hist[v];
+        if (lo < 0 && cum >= t_lo) lo = v;
+        if (hi < 0 && cum >= t_hi) hi = v;
+    }
+    free(hist);
+    for (long i = 0; i < N; ++i) {
+        if (lo == hi) {
+            out[i] = x[i];
+            continue;
+        }
+        long c = x[i] < lo ? lo : (x[i] > hi ? hi : x[i]);
+        /* floor(p/q + 1/2) = floor((2p + q) / (2q)) for p = (c - lo) * maxv, q = hi - lo */
+        const uint64_t p = (uint64_t)(c - lo) * (uint64_t)maxv, q = (uint64_t)(hi - lo);
+        out[i] = (uint16_t)((2 * p + q) / (2 * q));
+    }
+    if (lohi) {
+        lohi[0] = lo;
+        lohi[1] = hi;
+    }
+    return ORACLE_OK;
 }

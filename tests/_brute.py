@@ -83,3 +83,23 @@ def wiener_exact(f, w, noise_var=None, border_zero=False):
             else:
                 y_out[y, x] = mu[y][x] + max(s2 - nu2, 0) / den * (int(f[y, x]) - mu[y][x])
     return y_out, nu2, var
+
+
+def contrast_brute(x, bits, tol):
+    """Contrast stretch from the sorted pixel list: lo and hi are the k-th
+    smallest and k-th largest values, k = floor(tol * N); the map is rounded
+    half up with exact fractions.  Returns (out, lo, hi)."""
+    import math
+    x = np.asarray(x)
+    vals = sorted(int(v) for v in x.ravel())
+    n = len(vals)
+    k = math.floor(tol * n)
+    lo, hi = vals[k], vals[n - 1 - k]
+    if lo == hi:
+        return x.astype(np.int64), lo, hi
+    maxv = (1 << bits) - 1
+    out = np.empty(x.shape, dtype=np.int64)
+    for idx, v in np.ndenumerate(x):
+        c = min(max(int(v), lo), hi)
+        out[idx] = math.floor(Fraction((c - lo) * maxv, hi - lo) + Fraction(1, 2))
+    return out, lo, hi

@@ -12,6 +12,14 @@ Wiener (Algorithm 1, step 4d, local-statistics form):
   * limits: nu2 = 0 gives the identity, huge nu2 gives the box mean,
   * library routine scipy.signal.wiener with zero borders,
   * the binary32 twin within maxv * 2^-20 of binary64.
+Contrast stretch (Algorithm 1, step 4e; the rule is a reading, the paper
+gives none):
+  * hand-derived worked examples (tests/golden/contrast_worked_examples.json),
+  * the limits as order statistics of the sorted pixel list, and the map in
+    exact fractions, on random tiny images,
+  * closed forms: full-range ramp, affine ramps, two levels, constants,
+  * invariants: order preserved, at most k pixels beyond each limit, the
+    stretched range reaches 0 and maxv.
 """
 import json
 import os
@@ -21,9 +29,10 @@ import numpy as np
 import pytest
 
 import oracle
-from tests._brute import amf_brute, local_stats_exact, wiener_exact
+from tests._brute import amf_brute, contrast_brute, local_stats_exact, wiener_exact
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "amf_worked_examples.json")
+GOLDEN_CONTRAST = os.path.join(os.path.dirname(__file__), "golden", "contrast_worked_examples.json")
 
 
 # --------------------------------------------------------------------------- AMF
@@ -305,3 +314,78 @@ def test_hybrid_is_wiener_of_amf():
     np.testing.assert_array_equal(f, oracle.amf(g, 7))
     r2 = oracle.wiener(f, 3)
     np.testing.assert_array_equal(r.out64, r2.out64)
+
+
+# --------------------------------------------------------------------------- contrast stretch
+def test_contrast_golden_worked_examples():
+    for c in json.load(open(GOLDEN_CONTRAST))["cases"]:
+        dt = np.uint8 if c["bits"] == 8 else np.uint16
+        x = np.array(c["image"], dtype=dt)
+        out, lo, hi = oracle.contrast(x, c["tol"], bits=c["bits"])
+        assert (lo, hi) == (c["lo"], c["hi"]), c["name"]
+        np.testing.assert_array_equal(out, np.array(c["expected"]), err_msg=c["name"])
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_contrast_matches_sorted_brute(seed):
+    rng = np.random.default_rng(seed)
+    bits = int(rng.choice([3, 8, 10, 12, 16]))
+    dt = np.uint8 if bits <= 8 and rng.random() < 0.5 else np.uint16
+    H, W = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+    levels = int(rng.integers(1, 6)) if rng.random() < 0.4 else (1 << bits)
+    x = (rng.integers(0, levels, size=(H, W)) * ((1 << bits) // max(levels, 1))).clip(0, (1 << bits) - 1)
+    x = x.astype(dt)
+    tol = float(rng.choice([0.0, 0.01, 0.1, 0.2, 0.25, 1 / 3, 0.49]))
+    out, lo, hi = oracle.contrast(x, tol, bits=bits)
+    ref, rlo, rhi = contrast_brute(x, bits, tol)
+    assert (lo, hi) == (rlo, rhi)
+    np.testing.assert_array_equal(out.astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("bits", [8, 12, 16])
+def test_contrast_closed_forms(bits):
+    maxv = (1 << bits) - 1
+    dt = np.uint8 if bits == 8 else np.uint16
+    # the full-range ramp is already stretched: identity for tol = 0
+    ramp = np.arange(maxv + 1, dtype=np.int64).astype(dt).reshape(1, -1)
+    np.testing.assert_array_equal(oracle.contrast(ramp, 0.0, bits=bits)[0], ramp)
+    # an affine ramp a + b r, r = 0..m, maps to round-half-up(r maxv / m)
+    for a, b, m in ((3, 2, 50), (100, 1, 7), (0, 5, 1)):
+        r = np.arange(m + 1)
+        x = (a + b * r).astype(dt).reshape(1, -1)
+        want = (2 * r * maxv + m) // (2 * m)
+        out, lo, hi = oracle.contrast(x, 0.0, bits=bits)
+        assert (lo, hi) == (a, a + b * m)
+        np.testing.assert_array_equal(out.astype(np.int64).ravel(), want)
+    # two levels go to the two ends; constants and single pixels stay
+    two = np.array([[9, 40, 40, 9, 9]], dtype=dt)
+    np.testing.assert_array_equal(oracle.contrast(two, 0.0, bits=bits)[0], [[0, maxv, maxv, 0, 0]])
+    for v in (0, 1, maxv):
+        c = np.full((3, 4), v, dtype=dt)
+        np.testing.assert_array_equal(oracle.contrast(c, 0.3, bits=bits)[0], c)
+        np.testing.assert_array_equal(oracle.contrast(c[:1, :1], 0.0, bits=bits)[0], c[:1, :1])
+
+
+@pytest.mark.parametrize("tol", [0.0, 0.01, 0.05, 0.3])
+def test_contrast_invariants(tol):
+    rng = np.random.default_rng(11)
+    for bits, dt in ((8, np.uint8), (12, np.uint16)):
+        maxv = (1 << bits) - 1
+        x = np.clip(rng.normal(maxv * 0.4, maxv * 0.1, size=(37, 53)), 0, maxv).astype(dt)
+        out, lo, hi = oracle.contrast(x, tol, bits=bits)
+        k = int(np.floor(tol * x.size))
+        assert (x < lo).sum() <= k and (x > hi).sum() <= k
+        assert (x <= lo).sum() >= k + 1 and (x >= hi).sum() >= k + 1
+        assert lo < hi and out.min() == 0 and out.max() == maxv
+        order = np.argsort(x.ravel(), kind="stable")
+        assert (np.diff(out.ravel()[order].astype(np.int64)) >= 0).all()   # order preserved
+        assert (out[x <= lo] == 0).all() and (out[x >= hi] == maxv).all()
+
+
+def test_contrast_rejects_bad_arguments():
+    x = np.zeros((2, 2), np.uint8)
+    for tol in (-0.1, 0.5, 0.7, float("nan")):
+        with pytest.raises(oracle.OracleError):
+            oracle.contrast(x, tol)
+    with pytest.raises(oracle.OracleError):
+        oracle.contrast(np.array([[5000]], np.uint16), 0.0, bits=12)     # above 2^bits - 1
