@@ -13,6 +13,9 @@ Workloads (seeded synthetic phantoms, see synth/):
   stress4096 4096x4096 12-bit, sigma 40, density 0.40, Smax 11, 5x5 Wiener.
   batched    256 uneven 12-bit slices (256^2..1024^2), per-slice parameters,
              one persistent launch replayed as a CUDA graph.
+With --stretch TOL a single-image step also runs the contrast stretch of
+Algorithm 1, step 4e (contrast_stretch, in place on the result): the paper's
+whole step 4.  The contrast kernel is then also timed alone.
 
 Timing: W untimed warm-up steps, then K steps between barrier +
 synchronize, timed with CUDA events on the launching stream.  Inputs rotate
@@ -61,24 +64,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the persistent kernel's sources (the counters in profiles/ refer to it)."""
+def kernel_source_hash(files=("hd_kernel.cu", "hd_internal.h")) -> str:
+    """Hash of a kernel's sources (the counters in profiles/ refer to it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_05371_gb300", "csrc")
-    for name in ("hd_kernel.cu", "hd_internal.h"):
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch from an ncu capture, if taken on the current kernel source."""
+def recorded_traffic(workload: str, source: str | None = None):
+    """DRAM bytes per launch from an ncu capture, if taken on the current kernel source
+    (`source`: the kernel's file; default the persistent kernel)."""
     if not os.path.exists(PROFILE_TRAFFIC):
         return None
     with open(PROFILE_TRAFFIC) as fh:
         rec = json.load(fh)
     ent = rec.get(workload)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    want = kernel_source_hash((source,)) if source else kernel_source_hash()
+    if not ent or ent.get("source_hash") != want:
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -185,16 +190,20 @@ def build_workload(name: str, rank: int):
     raise SystemExit(f"unknown workload {name}")
 
 
-def describe(name: str, items) -> dict:
+def describe(name: str, items, stretch: float | None = None) -> dict:
     px = sum(s.H * s.W for s, _ in items)
     if name == "batched":
         return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
                             "density U[0.01,0.5], Smax {5,7,9,11}, Wiener {3,5,7}, one persistent launch "
                             "(CUDA graph)", "images": len(items), "megapixels": round(px / 1e6, 3)}
     s = items[0][0]
-    return {"workload": f"{name}: {s.H}x{s.W} {s.dtype} {s.bits}-bit, sigma {s.sigma:g}, s&p {s.density:g}, "
-                        f"Smax {s.smax}, Wiener {s.wiener_w}x{s.wiener_w}, noise variance estimated",
-            "H": s.H, "W": s.W, "smax": s.smax, "wiener_w": s.wiener_w, "megapixels": round(px / 1e6, 3)}
+    d = {"workload": f"{name}: {s.H}x{s.W} {s.dtype} {s.bits}-bit, sigma {s.sigma:g}, s&p {s.density:g}, "
+                     f"Smax {s.smax}, Wiener {s.wiener_w}x{s.wiener_w}, noise variance estimated",
+         "H": s.H, "W": s.W, "smax": s.smax, "wiener_w": s.wiener_w, "megapixels": round(px / 1e6, 3)}
+    if stretch is not None:
+        d["workload"] += f", then contrast stretch (tol {stretch:g}) in place"
+        d["contrast_stretch_tol"] = stretch
+    return d
 
 
 def algorithmic_bytes(items) -> int:
@@ -203,16 +212,22 @@ def algorithmic_bytes(items) -> int:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_sample_rate(items, budget_s: float):
-    """Oracle Mpx/s on a bounded sample: whole images (or row bands) until ~budget_s."""
+def oracle_sample_rate(items, budget_s: float, stretch: float | None = None):
+    """Oracle Mpx/s on a bounded sample: whole images (or row bands) until ~budget_s.
+    With `stretch`, each band's result also goes through the oracle's contrast stretch."""
     import oracle
+
+    def run(g, spec):
+        _, r = oracle.hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits)
+        if stretch is not None:
+            oracle.contrast(r.out32, stretch, bits=spec.bits)
     done_px, t_total = 0, 0.0
     descr = []
     for spec, g in items:
         # calibrate on a 32-row band, then size the band to the remaining budget
         rows = min(spec.H, 32)
         t0 = time.perf_counter()
-        oracle.hybrid(g[:rows], spec.smax, spec.wiener_w, bits=spec.bits)
+        run(g[:rows], spec)
         dt = time.perf_counter() - t0
         done_px += rows * spec.W
         t_total += dt
@@ -224,7 +239,7 @@ def oracle_sample_rate(items, budget_s: float):
         more = int(min(spec.H, max(1, remaining / per_row)))
         if more > rows:
             t0 = time.perf_counter()
-            oracle.hybrid(g[:more], spec.smax, spec.wiener_w, bits=spec.bits)
+            run(g[:more], spec)
             t_total += time.perf_counter() - t0
             done_px += more * spec.W
             rows = more
@@ -242,10 +257,10 @@ def run_reference(args, rank, world):
     items = build_workload(args.workload, 0)
     per_step = max(0.2, min(5.0, args.ref_budget / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample_rate(items, per_step)
+        oracle_sample_rate(items, per_step, args.stretch)
     rates, tsum, descr = [], 0.0, ""
     for _ in range(args.steps):
-        r, t, descr = oracle_sample_rate(items, per_step)
+        r, t, descr = oracle_sample_rate(items, per_step, args.stretch)
         rates.append(r)
         tsum += t
     value = statistics.median(rates)
@@ -255,7 +270,7 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * px_step / value, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8" if items[0][0].dtype == "u8" else "u16", "data": "synthetic",
-        "config": describe(args.workload, items),
+        "config": describe(args.workload, items, args.stretch),
         "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                          "sample": f"per step ~{per_step:.1f} s of the C oracle (single thread) on {descr}"},
         "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -369,7 +384,11 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=90.0, help="total seconds of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--stretch", type=float, default=None,
+                    help="also run the contrast stretch (Algorithm 1, step 4e) with this tolerance every step")
     args = ap.parse_args()
+    if args.stretch is not None and args.workload in ("batched", "served"):
+        raise SystemExit("--stretch applies to the single-image workloads")
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
@@ -393,7 +412,7 @@ def main():
         return run_served(args, rank, world, dev, hd, torch)
 
     items = build_workload(args.workload, rank)
-    cfg = describe(args.workload, items)
+    cfg = describe(args.workload, items, args.stretch)
     # work-item shape from the autotuner's table (paper_2005_05371_gb300/tuning.json)
     from paper_2005_05371_gb300 import autotune
     if args.workload == "batched":
@@ -449,13 +468,29 @@ def main():
         code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
         ws = hd._workspace(hd.hybrid_workspace_size(spec.H, spec.W, code, p), dev)
 
-        def step(i, s):
+        def hybrid_step(i, s):
             j = i % copies
             hd.hybrid_denoise(srcs[j], dsts[j], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
                               workspace=ws, stream=s)
 
+        step = hybrid_step
         launches_per_step = 1
         plain_step = None
+        if args.stretch is not None:
+            cws = hd._workspace(hd.contrast_workspace_size(spec.H, spec.W, code, spec.bits), dev)
+            cdsts = [torch.empty_like(srcs[0]) for _ in range(copies)]
+
+            def step(i, s):
+                hybrid_step(i, s)
+                j = i % copies
+                hd.contrast_stretch(dsts[j], None, args.stretch, p.bits, workspace=cws, stream=s)
+
+            def contrast_step(i, s):
+                # the stretch alone, dsts -> cdsts (same data every time around)
+                j = i % copies
+                hd.contrast_stretch(dsts[j], cdsts[j], args.stretch, p.bits, workspace=cws, stream=s)
+
+            launches_per_step = 2
 
     use_graph = args.workload != "batched"
 
@@ -533,17 +568,34 @@ def main():
     ms_per_step = total_ms / args.steps
     value = weak_value(px_per_step, args.steps, total_ms, world)
 
-    # dominant (and only) kernel: one persistent launch per step; events over
+    # dominant kernel: one persistent launch per step; events over
     # back-to-back launches (graph replay) give the average launch duration
     peak, peak_kind = peaks()
-    achieved = step_bytes / (ms_per_step / 1e3) / 1e9
+    extra = {}
+    hybrid_ms = ms_per_step
+    if args.stretch is not None:
+        # each kernel alone, same launch configuration and rotation of copies
+        K2 = max(10, args.steps)
+        h_ms, _, _ = timed(hybrid_step, K2, args.warmup, True)
+        c_ms, _, _ = timed(contrast_step, K2, args.warmup, True)
+        hybrid_ms, contrast_ms = max_over_ranks(h_ms, dev) / K2, max_over_ranks(c_ms, dev) / K2
+        c_ach = step_bytes / (contrast_ms / 1e3) / 1e9
+        extra["contrast_kernel"] = {"kernel": "contrast_kernel", "ms": round(contrast_ms, 5),
+                                    "bound": "hbm", "achieved": round(c_ach, 1), "peak": peak, "unit": "GB/s",
+                                    "frac": round(c_ach / peak, 4), "traffic": recorded_traffic(
+                                        args.workload + "_contrast", "hd_contrast.cu"),
+                                    "algorithmic_bytes_per_launch": step_bytes,
+                                    "hybrid_kernel_ms": round(hybrid_ms, 5)}
+        status = hd.hd_get_device_error(stream)
+        if status != hd.HD_OK:
+            raise SystemExit(f"device error in the per-kernel timing: {hd.hd_status_str(status)}")
+    achieved = step_bytes / (hybrid_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
                 "kernel": "hd_persistent_kernel", "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": step_bytes}
 
-    extra = {}
     if plain_step is not None:
         plain_ms, _, _ = timed(plain_step, max(3, args.steps // 5), args.warmup, False)
         extra["plain_loop"] = {"value": round(px_per_step * max(3, args.steps // 5) / (plain_ms / 1e3) / 1e6, 1),
@@ -551,7 +603,30 @@ def main():
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e and args.workload != "batched":
+    if not args.no_e2e and args.stretch is not None:
+        # end to end through the public calls: pinned host -> device, hybrid,
+        # stretch, device -> pinned host, wait
+        spec, g = items[0]
+        hsrc = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory()
+        hdst = torch.empty_like(hsrc).pin_memory()
+
+        def e2e_step(i):
+            srcs[0].copy_(hsrc, non_blocking=True)
+            hd.hybrid_denoise(srcs[0], dsts[0], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                              workspace=ws, stream=stream)
+            hd.contrast_stretch(dsts[0], None, args.stretch, p.bits, workspace=cws, stream=stream)
+            hdst.copy_(dsts[0], non_blocking=True)
+            stream.synchronize()
+        for i in range(args.warmup):
+            e2e_step(i)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_step(i)
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(world * px_per_step * args.steps / dt / 1e6, 2), "unit": "Mpixel/s",
+               "h2d_bytes_per_step": g.nbytes, "d2h_bytes_per_step": g.nbytes,
+               "api": "copy_ + hybrid_denoise + contrast_stretch (pinned host buffers)"}
+    elif not args.no_e2e and args.workload != "batched":
         spec, g = items[0]
         p = params_of(spec)
         code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
@@ -602,7 +677,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget)
+        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget, args.stretch)
         cpu = {"value": round(rate, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                "sample": f"C oracle, single thread, {secs:.1f} s on {descr}"}
 

@@ -16,7 +16,7 @@
  *     host pointers there).  The library allocates no device memory.
  *   - src and dst must not overlap: the adaptive median reads only the noisy
  *     input (the listing's neighbourhood statistics are taken of g, never of
- *     the partly filtered copy).
+ *     the partly filtered copy).  contrast_stretch alone also runs in place.
  *   - Work is enqueued on `stream` (NULL = legacy default stream).  Argument
  *     errors are returned synchronously before anything is enqueued.  Launch
  *     failures return HD_ERR_CUDA.  Faults seen by the kernels while running
@@ -174,6 +174,32 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
  * Same filtering, parameters, errors and output as hybrid_denoise. */
 #define HD_STATIC_SCRATCH_BYTES (36u * 1024u * 1024u)
 hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
+
+/* ---------------------------------------------------------------- contrast
+ * Contrast stretch, the post-processing step of the hybrid (Algorithm 1,
+ * step 4e).  The paper gives no rule; this is a linear stretch between two
+ * saturation limits taken from the image histogram, with at most k pixels
+ * saturating at each end:
+ *   k  = floor(fl64(tol * N)), N = H * W, 0 <= tol < 0.5 (tol = 0: min-max),
+ *   lo = the k-th smallest pixel value (counting from 0), hi = the k-th largest,
+ *   dst = src where lo == hi, else
+ *   dst = floor((clamp(src, lo, hi) - lo) * maxv / (hi - lo) + 1/2),
+ * maxv = 2^bits - 1, in exact integer arithmetic (round half up).  Values
+ * above maxv are outside the contract (they count as maxv).
+ *   img: src and dst device images of the same size and dtype; dst == src with
+ *        the same pitch runs in place; any other overlap is HD_ERR_ARG.  Only
+ *        img->p.bits is used; noise_var_out and y_out are ignored.
+ *   tol: outside [0, 0.5) or NaN is HD_ERR_ARG.
+ *   workspace: device, 256-byte aligned, >= contrast_workspace_size() bytes
+ *        (a 256-byte control block and a 2^bits-entry histogram), zero-filled
+ *        before first use; each call leaves it zeroed.
+ * One kernel launch.  Its CTAs wait for one another (bounded): a wait that
+ * runs out (e.g. when other work holds the GPU's SMs so long that the grid is
+ * not resident at once) latches HD_ERR_TIMEOUT for hd_get_device_error and
+ * leaves dst unwritten. */
+hd_status contrast_stretch(const hd_image *img, double tol, void *workspace, size_t ws_bytes,
+                           hd_stream_t stream);
+hd_status contrast_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
 /* ---------------------------------------------------------------- batches
  * Many images of uneven sizes and per-image parameters in ONE persistent

@@ -8,7 +8,8 @@ for device memory and streams only.  If the library is missing or cannot be
 loaded the import fails loudly; there is no CPU fallback.
 
 Algorithm (Youssef, Mahmoud, El-Horbaty): adaptive median (Algorithm 1,
-step 6) followed by a local-statistics Wiener filter (Algorithm 1, step 4d).
+step 6) followed by a local-statistics Wiener filter (Algorithm 1, step 4d),
+and the contrast stretch of step 4e as a separate call.
 """
 from __future__ import annotations
 
@@ -35,7 +36,7 @@ EXPORTS = [
     "hybrid_min_workspace_size", "hybrid_denoise_host", "hybrid_host_workspace_size", "hybrid_denoise_static", "hybrid_denoise_batched",
     "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
-    "hd_status_str", "hd_version",
+    "hd_status_str", "hd_version", "contrast_stretch", "contrast_workspace_size",
 ]
 
 
@@ -87,6 +88,8 @@ def _load() -> ctypes.CDLL:
         "hd_get_tuning": ([ctypes.POINTER(hd_tuning)], I),
         "hd_set_spin_limit": ([ctypes.c_ulonglong], I),
         "hd_get_device_error": ([P], I),
+        "contrast_stretch": ([img_p, ctypes.c_double, P, S, P], I),
+        "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
         "hd_version": ([], I),
     }
@@ -242,6 +245,26 @@ def wiener_filter(src, dst, wiener_w: int = 5, noise_var: float = -1.0, border: 
         workspace = _workspace(wiener_workspace_size(img.H, img.W, img.dtype, p), src.device)
     _check(_lib.wiener_filter(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace), _stream_ptr(stream)),
            "wiener_filter")
+    return dst
+
+
+def contrast_workspace_size(H: int, W: int, dtype_code: int, bits: int | None = None) -> int:
+    n = ctypes.c_size_t()
+    p = Params(bits=bits).to_c(dtype_code)
+    _check(_lib.contrast_workspace_size(H, W, dtype_code, ctypes.byref(p), ctypes.byref(n)),
+           "contrast_workspace_size")
+    return n.value
+
+
+def contrast_stretch(src, dst=None, tol: float = 0.01, bits: int | None = None, workspace=None, stream=None):
+    """Contrast stretch (Algorithm 1, step 4e) of ``src`` into ``dst`` (in place when ``dst`` is None)."""
+    if dst is None:
+        dst = src
+    img = make_image(src, dst, Params(bits=bits))
+    if workspace is None:
+        workspace = _workspace(contrast_workspace_size(img.H, img.W, img.dtype, bits), src.device)
+    _check(_lib.contrast_stretch(ctypes.byref(img), float(tol), _ws_ptr(workspace), _ws_len(workspace),
+                                 _stream_ptr(stream)), "contrast_stretch")
     return dst
 
 

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "hd_contrast.h"
 #include "hd_internal.h"
 #include "hybrid_denoise.h"
 
@@ -28,6 +29,16 @@ inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 std::mutex g_tune_mu;
 hd_tuning g_tune = {32, 0, 0};
 unsigned long long g_spin_limit = kSpinLimit;
+
+}  // namespace
+
+unsigned long long hd::spin_limit_polls()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_spin_limit;
+}
+
+namespace {
 
 hd_tuning current_tuning()
 {
@@ -595,9 +606,10 @@ hd_status hd_set_spin_limit(unsigned long long polls)
 hd_status hd_get_device_error(hd_stream_t stream)
 {
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return HD_ERR_CUDA;
-    unsigned int v = 0;
+    unsigned int v = 0, vc = 0;
     if (read_and_clear_device_error(&v) != 0) return HD_ERR_CUDA;
-    if (v & DEVERR_TIMEOUT) return HD_ERR_TIMEOUT;
+    if (read_and_clear_contrast_error(&vc) != 0) return HD_ERR_CUDA;
+    if ((v | vc) & DEVERR_TIMEOUT) return HD_ERR_TIMEOUT;
     return HD_OK;
 }
 
