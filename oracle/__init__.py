@@ -15,6 +15,12 @@ What each function follows in the paper:
                      mean local variance unless supplied).
 * ``hybrid``       - Algorithm 1, step 4: Wiener(AMF(g)).  The contrast
                      stretch of step 4e is the separate ``contrast``.
+* ``amf_strips`` / ``hybrid_strips`` - Algorithm 1, step 6 as the listing
+                     partitions it: the image is cut into ``parts`` row strips
+                     (rows floor(i H / parts) .. floor((i+1) H / parts) - 1)
+                     and each strip is median-filtered alone, its borders
+                     reflected at the strip's own edges; the Wiener filter then
+                     runs on the whole reassembled image.
 * ``contrast``     - Algorithm 1, step 4e (the paper gives no rule): linear
                      stretch between the k-th smallest and k-th largest
                      values, k = floor(tol * N), exact integer rounding.
@@ -192,6 +198,32 @@ def hybrid(g: np.ndarray, smax: int, w: int, noise_var: float = -1.0, bits: int 
     Returns (f, WienerResult) where f is the adaptive-median output.
     """
     f = amf(g, smax, keep_unresolved=keep_unresolved)
+    return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero)
+
+
+def strip_bounds(H: int, parts: int) -> list[int]:
+    """Row boundaries of the listing's image partition: strip i covers rows
+    [b[i], b[i+1]), b[i] = floor(i * H / parts)."""
+    if not (1 <= parts <= H):
+        raise ValueError("parts must be in [1, H]")
+    return [(i * H) // parts for i in range(parts + 1)]
+
+
+def amf_strips(g: np.ndarray, smax: int, parts: int, keep_unresolved: bool = False) -> np.ndarray:
+    """Adaptive median of each row strip alone (Algorithm 1, step 6, with the
+    listing's ``parts`` partitions): windows reflect at each strip's edges."""
+    b = strip_bounds(g.shape[0], parts)
+    f = np.empty_like(g)
+    for i in range(parts):
+        f[b[i]:b[i + 1]] = amf(g[b[i]:b[i + 1]], smax, keep_unresolved=keep_unresolved)
+    return f
+
+
+def hybrid_strips(g: np.ndarray, smax: int, w: int, parts: int, noise_var: float = -1.0,
+                  bits: int | None = None, keep_unresolved: bool = False, border_zero: bool = False):
+    """Algorithm 1, step 4 with a partitioned median: Wiener of the whole image
+    assembled from the strips' medians.  Returns (f, WienerResult)."""
+    f = amf_strips(g, smax, parts, keep_unresolved=keep_unresolved)
     return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero)
 
 

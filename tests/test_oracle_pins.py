@@ -12,6 +12,11 @@ Wiener (Algorithm 1, step 4d, local-statistics form):
   * limits: nu2 = 0 gives the identity, huge nu2 gives the box mean,
   * library routine scipy.signal.wiener with zero borders,
   * the binary32 twin within maxv * 2^-20 of binary64.
+Partitioned median (Algorithm 1, step 6 with `parts` strips):
+  * a hand-derived seam example (tests/golden/strips_worked_examples.json),
+  * every strip equals the brute-force median of that strip alone,
+  * one part is the whole-image median; rows whose Smax window stays inside
+    their strip equal the whole-image median rows.
 Contrast stretch (Algorithm 1, step 4e; the rule is a reading, the paper
 gives none):
   * hand-derived worked examples (tests/golden/contrast_worked_examples.json),
@@ -33,6 +38,7 @@ from tests._brute import amf_brute, contrast_brute, local_stats_exact, wiener_ex
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "amf_worked_examples.json")
 GOLDEN_CONTRAST = os.path.join(os.path.dirname(__file__), "golden", "contrast_worked_examples.json")
+GOLDEN_STRIPS = os.path.join(os.path.dirname(__file__), "golden", "strips_worked_examples.json")
 
 
 # --------------------------------------------------------------------------- AMF
@@ -314,6 +320,50 @@ def test_hybrid_is_wiener_of_amf():
     np.testing.assert_array_equal(f, oracle.amf(g, 7))
     r2 = oracle.wiener(f, 3)
     np.testing.assert_array_equal(r.out64, r2.out64)
+
+
+# --------------------------------------------------------------------------- partitioned median
+def test_strips_golden_worked_examples():
+    for c in json.load(open(GOLDEN_STRIPS))["cases"]:
+        g = np.array(c["image"], dtype=np.uint8)
+        assert oracle.strip_bounds(g.shape[0], c["parts"]) == c["bounds"], c["name"]
+        if "pixel" in c:
+            y, x = c["pixel"]
+            assert oracle.amf(g, c["smax"])[y, x] == c["whole_image"]
+            assert oracle.amf_strips(g, c["smax"], c["parts"])[y, x] == c["strips"]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_strips_match_brute_per_strip(seed):
+    rng = np.random.default_rng(seed)
+    H, W = int(rng.integers(1, 14)), int(rng.integers(1, 9))
+    parts = int(rng.integers(1, H + 1))
+    smax = int(rng.choice([3, 5, 7]))
+    g = rng.integers(0, 4, size=(H, W)).astype(np.uint8) * 60
+    f = oracle.amf_strips(g, smax, parts)
+    b = [(i * H) // parts for i in range(parts + 1)]
+    for i in range(parts):
+        want, _ = amf_brute(g[b[i]:b[i + 1]], smax)
+        np.testing.assert_array_equal(f[b[i]:b[i + 1]], want)
+
+
+@pytest.mark.parametrize("parts", [1, 2, 3, 8])
+def test_strips_locality(parts):
+    g = np.random.default_rng(parts).integers(0, 256, size=(64, 40)).astype(np.uint8)
+    smax = 7
+    f = oracle.amf_strips(g, smax, parts)
+    whole = oracle.amf(g, smax)
+    if parts == 1:
+        np.testing.assert_array_equal(f, whole)
+        _, r1 = oracle.hybrid_strips(g, smax, 5, 1)
+        _, r2 = oracle.hybrid(g, smax, 5)
+        np.testing.assert_array_equal(r1.out32, r2.out32)
+    b = oracle.strip_bounds(64, parts)
+    inner = [y for y in range(64) if all(abs(y - s) >= smax // 2 and abs(y - (s - 1)) >= smax // 2
+                                         for s in b[1:-1])]
+    np.testing.assert_array_equal(f[inner], whole[inner])
+    if parts > 1:
+        assert (f != whole).any()          # the seams do change some pixels
 
 
 # --------------------------------------------------------------------------- contrast stretch
