@@ -13,6 +13,9 @@ Workloads (seeded synthetic phantoms, see synth/):
   stress4096 4096x4096 12-bit, sigma 40, density 0.40, Smax 11, 5x5 Wiener.
   batched    256 uneven 12-bit slices (256^2..1024^2), per-slice parameters,
              one persistent launch replayed as a CUDA graph.
+With --parts P a single-image step runs the listing's partitioned median
+(hybrid_denoise_strips: P row strips median-filtered alone, then the Wiener
+filter of the whole image), as the paper runs it with P workers.
 With --stretch TOL a single-image step also runs the contrast stretch of
 Algorithm 1, step 4e (contrast_stretch, in place on the result): the paper's
 whole step 4.  The contrast kernel is then also timed alone.
@@ -190,7 +193,7 @@ def build_workload(name: str, rank: int):
     raise SystemExit(f"unknown workload {name}")
 
 
-def describe(name: str, items, stretch: float | None = None) -> dict:
+def describe(name: str, items, stretch: float | None = None, parts: int = 1) -> dict:
     px = sum(s.H * s.W for s, _ in items)
     if name == "batched":
         return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
@@ -200,6 +203,9 @@ def describe(name: str, items, stretch: float | None = None) -> dict:
     d = {"workload": f"{name}: {s.H}x{s.W} {s.dtype} {s.bits}-bit, sigma {s.sigma:g}, s&p {s.density:g}, "
                      f"Smax {s.smax}, Wiener {s.wiener_w}x{s.wiener_w}, noise variance estimated",
          "H": s.H, "W": s.W, "smax": s.smax, "wiener_w": s.wiener_w, "megapixels": round(px / 1e6, 3)}
+    if parts > 1:
+        d["workload"] += f", median partitioned into {parts} row strips"
+        d["parts"] = parts
     if stretch is not None:
         d["workload"] += f", then contrast stretch (tol {stretch:g}) in place"
         d["contrast_stretch_tol"] = stretch
@@ -212,13 +218,17 @@ def algorithmic_bytes(items) -> int:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_sample_rate(items, budget_s: float, stretch: float | None = None):
+def oracle_sample_rate(items, budget_s: float, stretch: float | None = None, parts: int = 1):
     """Oracle Mpx/s on a bounded sample: whole images (or row bands) until ~budget_s.
-    With `stretch`, each band's result also goes through the oracle's contrast stretch."""
+    With `stretch`, each band's result also goes through the oracle's contrast
+    stretch; with `parts` > 1 the band's median is partitioned."""
     import oracle
 
     def run(g, spec):
-        _, r = oracle.hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits)
+        if parts > 1:
+            _, r = oracle.hybrid_strips(g, spec.smax, spec.wiener_w, min(parts, g.shape[0]), bits=spec.bits)
+        else:
+            _, r = oracle.hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits)
         if stretch is not None:
             oracle.contrast(r.out32, stretch, bits=spec.bits)
     done_px, t_total = 0, 0.0
@@ -257,10 +267,10 @@ def run_reference(args, rank, world):
     items = build_workload(args.workload, 0)
     per_step = max(0.2, min(5.0, args.ref_budget / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample_rate(items, per_step, args.stretch)
+        oracle_sample_rate(items, per_step, args.stretch, args.parts)
     rates, tsum, descr = [], 0.0, ""
     for _ in range(args.steps):
-        r, t, descr = oracle_sample_rate(items, per_step, args.stretch)
+        r, t, descr = oracle_sample_rate(items, per_step, args.stretch, args.parts)
         rates.append(r)
         tsum += t
     value = statistics.median(rates)
@@ -270,7 +280,7 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * px_step / value, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8" if items[0][0].dtype == "u8" else "u16", "data": "synthetic",
-        "config": describe(args.workload, items, args.stretch),
+        "config": describe(args.workload, items, args.stretch, args.parts),
         "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                          "sample": f"per step ~{per_step:.1f} s of the C oracle (single thread) on {descr}"},
         "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -384,11 +394,15 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=90.0, help="total seconds of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--parts", type=int, default=1,
+                    help="row strips of the partitioned median (Algorithm 1, step 6); 1 = whole image")
     ap.add_argument("--stretch", type=float, default=None,
                     help="also run the contrast stretch (Algorithm 1, step 4e) with this tolerance every step")
     args = ap.parse_args()
-    if args.stretch is not None and args.workload in ("batched", "served"):
-        raise SystemExit("--stretch applies to the single-image workloads")
+    if (args.stretch is not None or args.parts > 1) and args.workload in ("batched", "served"):
+        raise SystemExit("--stretch and --parts apply to the single-image workloads")
+    if args.parts < 1:
+        raise SystemExit("--parts must be >= 1")
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
@@ -412,7 +426,7 @@ def main():
         return run_served(args, rank, world, dev, hd, torch)
 
     items = build_workload(args.workload, rank)
-    cfg = describe(args.workload, items, args.stretch)
+    cfg = describe(args.workload, items, args.stretch, args.parts)
     # work-item shape from the autotuner's table (paper_2005_05371_gb300/tuning.json)
     from paper_2005_05371_gb300 import autotune
     if args.workload == "batched":
@@ -466,15 +480,25 @@ def main():
         srcs = [to_dev(g) for _ in range(copies)]
         dsts = [torch.empty_like(srcs[0]) for _ in range(copies)]
         code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
-        ws = hd._workspace(hd.hybrid_workspace_size(spec.H, spec.W, code, p), dev)
+        if args.parts > 1:
+            ws = hd._workspace(hd.hybrid_strips_workspace_size(spec.H, spec.W, code, p, args.parts), dev)
 
-        def hybrid_step(i, s):
-            j = i % copies
-            hd.hybrid_denoise(srcs[j], dsts[j], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
-                              workspace=ws, stream=s)
+            def hybrid_step(i, s):
+                j = i % copies
+                hd.hybrid_denoise_strips(srcs[j], dsts[j], args.parts, p.smax, p.wiener_w, p.noise_var, p.border,
+                                         p.unresolved, p.bits, workspace=ws, stream=s)
+            # strip medians, descriptor upload, Wiener
+            launches_per_step = 3
+        else:
+            ws = hd._workspace(hd.hybrid_workspace_size(spec.H, spec.W, code, p), dev)
+
+            def hybrid_step(i, s):
+                j = i % copies
+                hd.hybrid_denoise(srcs[j], dsts[j], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved,
+                                  p.bits, workspace=ws, stream=s)
+            launches_per_step = 1
 
         step = hybrid_step
-        launches_per_step = 1
         plain_step = None
         if args.stretch is not None:
             cws = hd._workspace(hd.contrast_workspace_size(spec.H, spec.W, code, spec.bits), dev)
@@ -490,7 +514,7 @@ def main():
                 j = i % copies
                 hd.contrast_stretch(dsts[j], cdsts[j], args.stretch, p.bits, workspace=cws, stream=s)
 
-            launches_per_step = 2
+            launches_per_step += 1
 
     use_graph = args.workload != "batched"
 
@@ -603,7 +627,7 @@ def main():
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e and args.stretch is not None:
+    if not args.no_e2e and (args.stretch is not None or args.parts > 1):
         # end to end through the public calls: pinned host -> device, hybrid,
         # stretch, device -> pinned host, wait
         spec, g = items[0]
@@ -612,9 +636,9 @@ def main():
 
         def e2e_step(i):
             srcs[0].copy_(hsrc, non_blocking=True)
-            hd.hybrid_denoise(srcs[0], dsts[0], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
-                              workspace=ws, stream=stream)
-            hd.contrast_stretch(dsts[0], None, args.stretch, p.bits, workspace=cws, stream=stream)
+            hybrid_step(0, stream)
+            if args.stretch is not None:
+                hd.contrast_stretch(dsts[0], None, args.stretch, p.bits, workspace=cws, stream=stream)
             hdst.copy_(dsts[0], non_blocking=True)
             stream.synchronize()
         for i in range(args.warmup):
@@ -625,7 +649,8 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": round(world * px_per_step * args.steps / dt / 1e6, 2), "unit": "Mpixel/s",
                "h2d_bytes_per_step": g.nbytes, "d2h_bytes_per_step": g.nbytes,
-               "api": "copy_ + hybrid_denoise + contrast_stretch (pinned host buffers)"}
+               "api": "copy_ + " + ("hybrid_denoise_strips" if args.parts > 1 else "hybrid_denoise") +
+                      (" + contrast_stretch" if args.stretch is not None else "") + " (pinned host buffers)"}
     elif not args.no_e2e and args.workload != "batched":
         spec, g = items[0]
         p = params_of(spec)
@@ -677,9 +702,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget, args.stretch)
+        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget, args.stretch, args.parts)
         cpu = {"value": round(rate, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                "sample": f"C oracle, single thread, {secs:.1f} s on {descr}"}
+        # the paper's parallel metrics (Section 3.3): T_s = the serial oracle's
+        # time for one step's pixels, T_p = this GPU's step, P = its SMs
+        t_s = px_per_step / (rate * 1e6) * 1e3
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        s_p = t_s / ms_per_step
+        extra["paper_metrics"] = {"T_s_ms": round(t_s, 3), "T_p_ms": round(ms_per_step, 5), "P": n_sm,
+                                  "S_P": round(s_p, 1), "EFF": round(s_p / n_sm, 2),
+                                  "T_over_ms": round(ms_per_step - t_s / n_sm, 5),
+                                  "defs": "Eq. 1 S_P = T_s/T_p, Eq. 2 EFF = S_P/P, Eq. 3 T_over = T_p - T_s/P; "
+                                          "T_s: the C oracle on one host core, P: streaming multiprocessors"}
 
     if rank == 0:
         line = {

@@ -141,6 +141,25 @@ hd_status hybrid_denoise(const hd_image *img, void *workspace, size_t ws_bytes,
 hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
+/* The hybrid with the listing's partitioned median (Algorithm 1, step 6:
+ * parallelAdapMedian(g, Smax, parts)).  The image is cut into `parts` row
+ * strips, strip i covering rows floor(i H / parts) .. floor((i+1) H / parts) - 1,
+ * and each strip is median-filtered as an image of its own: its windows
+ * reflect at the strip's edges, so pixels within Smax/2 rows of a seam can
+ * differ from hybrid_denoise.  The Wiener filter then runs on the whole
+ * reassembled median image.  parts = 1 is exactly hybrid_denoise.
+ *   parts: 1..H, else HD_ERR_ARG.
+ *   workspace: device, 256-byte aligned, >= hybrid_strips_workspace_size()
+ *   bytes.  Each call clears the counters it uses first (a memset on the
+ *   stream), so one workspace serves calls of any size and partition in turn.
+ * Two persistent launches (all strips' medians in one, then the Wiener), plus
+ * the memset and one small launch that writes the strip descriptors into the
+ * workspace (parts = 1: the memset and hybrid_denoise's single launch). */
+hd_status hybrid_denoise_strips(const hd_image *img, int parts, void *workspace, size_t ws_bytes,
+                                hd_stream_t stream);
+hd_status hybrid_strips_workspace_size(int H, int W, int dtype, const hd_params *p, int parts,
+                                       size_t *bytes);
+
 /* The hybrid over host buffers: img->src and img->dst are HOST pointers
  * (pinned memory gives overlap-free full-speed copies; pageable works).  The
  * call copies src into the workspace, runs hybrid_denoise there, copies the

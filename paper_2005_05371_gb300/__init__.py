@@ -37,6 +37,7 @@ EXPORTS = [
     "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
     "hd_status_str", "hd_version", "contrast_stretch", "contrast_workspace_size",
+    "hybrid_denoise_strips", "hybrid_strips_workspace_size",
 ]
 
 
@@ -89,6 +90,8 @@ def _load() -> ctypes.CDLL:
         "hd_set_spin_limit": ([ctypes.c_ulonglong], I),
         "hd_get_device_error": ([P], I),
         "contrast_stretch": ([img_p, ctypes.c_double, P, S, P], I),
+        "hybrid_denoise_strips": ([img_p, I, P, S, P], I),
+        "hybrid_strips_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
         "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
         "hd_version": ([], I),
@@ -245,6 +248,28 @@ def wiener_filter(src, dst, wiener_w: int = 5, noise_var: float = -1.0, border: 
         workspace = _workspace(wiener_workspace_size(img.H, img.W, img.dtype, p), src.device)
     _check(_lib.wiener_filter(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace), _stream_ptr(stream)),
            "wiener_filter")
+    return dst
+
+
+def hybrid_strips_workspace_size(H: int, W: int, dtype_code: int, params: Params, parts: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_strips_workspace_size(H, W, dtype_code, ctypes.byref(params.to_c(dtype_code)), int(parts),
+                                             ctypes.byref(n)), "hybrid_strips_workspace_size")
+    return n.value
+
+
+def hybrid_denoise_strips(src, dst, parts: int, smax: int = 11, wiener_w: int = 5, noise_var: float = -1.0,
+                          border: int = HD_BORDER_SYMMETRIC, unresolved: int = HD_UNRESOLVED_ZMED,
+                          bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None):
+    """Hybrid with the listing's partitioned median: ``parts`` row strips
+    median-filtered alone, then the Wiener filter of the whole image
+    (Algorithm 1, steps 4 and 6)."""
+    p = Params(smax, wiener_w, noise_var, border, unresolved, bits)
+    img = make_image(src, dst, p, noise_var_out, y_out)
+    if workspace is None:
+        workspace = _workspace(hybrid_strips_workspace_size(img.H, img.W, img.dtype, p, parts), src.device)
+    _check(_lib.hybrid_denoise_strips(ctypes.byref(img), int(parts), _ws_ptr(workspace), _ws_len(workspace),
+                                      _stream_ptr(stream)), "hybrid_denoise_strips")
     return dst
 
 

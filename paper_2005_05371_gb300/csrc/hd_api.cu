@@ -357,6 +357,34 @@ std::vector<uint8_t> table_image(const BatchLayout &L, const BatchTables &bt)
     return h;
 }
 
+// ---------------------------------------------------------------- strips
+// The listing's partitioned median (Algorithm 1, step 6 with `parts`
+// sub-images): row strips [floor(i H / parts), floor((i+1) H / parts)), each
+// median-filtered as an image of its own (borders reflect at the strip's
+// edges), then the Wiener filter over the whole reassembled median image.
+// Workspace: [median queue counters][Wiener workspace: its counters and control
+// block, then the statistics plane when estimating][strip descriptors][strip
+// segments][median image].  The offsets move with the image size and `parts`,
+// so every call clears the control words it uses (one memset) before its
+// launches: a workspace can serve calls of any size and partition in turn.
+struct StripLayout {
+    size_t wiener_off, desc_off, seg_off, fbuf_off, total;
+    size_t control_bytes;     // [0, control_bytes) holds every counter of the call
+};
+
+StripLayout strip_layout(int H, int W, int dtype, const hd_params *p, int parts)
+{
+    StripLayout L;
+    L.wiener_off = round_up(kTicketBytes, kAlign);
+    L.control_bytes = L.wiener_off + ctl_bytes();
+    const size_t wiener_bytes = p->noise_var < 0.0 ? single_ws_full(H, W, dtype, false) : ctl_bytes();
+    L.desc_off = round_up(L.wiener_off + wiener_bytes, kAlign);
+    L.seg_off = round_up(L.desc_off + sizeof(ImgDesc) * (size_t)parts, kAlign);
+    L.fbuf_off = round_up(L.seg_off + sizeof(Seg) * (size_t)parts, kAlign);
+    L.total = L.fbuf_off + round_up((size_t)H * f_pitch_of(W, dtype), kAlign);
+    return L;
+}
+
 }  // namespace
 
 namespace hd {
@@ -483,6 +511,82 @@ hd_status hybrid_denoise_host(const hd_image *img, void *workspace, size_t ws_by
     if (eout != cudaSuccess) return HD_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return HD_ERR_CUDA;
     return HD_OK;
+}
+
+hd_status hybrid_strips_workspace_size(int H, int W, int dtype, const hd_params *p, int parts, size_t *bytes)
+{
+    if (!bytes || !p || H < 1 || W < 1) return HD_ERR_ARG;
+    if (dtype != HD_U8 && dtype != HD_U16) return HD_ERR_DTYPE;
+    if (parts < 1 || parts > H) return HD_ERR_ARG;
+    if (parts == 1) return hybrid_workspace_size(H, W, dtype, p, bytes);
+    *bytes = strip_layout(H, W, dtype, p, parts).total;
+    return HD_OK;
+}
+
+hd_status hybrid_denoise_strips(const hd_image *img, int parts, void *workspace, size_t ws_bytes,
+                                hd_stream_t stream)
+{
+    hd_status st = check_image(img, true, true, false);
+    if (st != HD_OK) return st;
+    if (parts < 1 || parts > img->H) return HD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (parts == 1) {
+        // the whole-image hybrid, on the same workspace: clear its counters first
+        if (workspace && ((uintptr_t)workspace % kAlign) == 0 && ws_bytes >= ctl_bytes() &&
+            cudaMemsetAsync(workspace, 0, ctl_bytes(), s) != cudaSuccess)
+            return HD_ERR_CUDA;
+        return run_single(img, hybrid_mode(img), workspace, ws_bytes, s);
+    }
+    const StripLayout L = strip_layout(img->H, img->W, img->dtype, &img->p, parts);
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return HD_ERR_WORKSPACE;
+    if (ws_bytes < L.total) return HD_ERR_WORKSPACE;
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    uint8_t *fbuf = base + L.fbuf_off;
+    const size_t f_pitch = f_pitch_of(img->W, img->dtype);
+    const hd_tuning t = current_tuning();
+
+    // the medians of all strips in one persistent launch
+    std::vector<uint8_t> tab(L.seg_off - L.desc_off + sizeof(Seg) * (size_t)parts, 0);
+    ImgDesc *descs = reinterpret_cast<ImgDesc *>(tab.data());
+    Seg *segs = reinterpret_cast<Seg *>(tab.data() + (L.seg_off - L.desc_off));
+    long long first = 0;
+    for (int i = 0; i < parts; ++i) {
+        const int y0 = (int)((long long)i * img->H / parts), y1 = (int)((long long)(i + 1) * img->H / parts);
+        hd_image si = *img;
+        si.src = static_cast<const uint8_t *>(img->src) + (size_t)y0 * img->src_pitch;
+        si.dst = fbuf + (size_t)y0 * f_pitch;
+        si.dst_pitch = f_pitch;
+        si.H = y1 - y0;
+        si.noise_var_out = nullptr;
+        si.y_out = nullptr;
+        descs[i] = make_desc(&si, MODE_AMF, t, nullptr, nullptr);
+        const int tiles = descs[i].tiles_x * descs[i].tiles_y;
+        segs[i] = Seg{i, 1, (int)first, tiles};
+        first += tiles;
+    }
+    if (first > 0x7fffffffLL) return HD_ERR_OVERFLOW;
+    LaunchParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.descs = reinterpret_cast<const ImgDesc *>(base + L.desc_off);
+    lp.segs = reinterpret_cast<const Seg *>(base + L.seg_off);
+    lp.nsegs = parts;
+    lp.total_items = (int)first;
+    lp.ticket = reinterpret_cast<unsigned int *>(base);
+    lp.ra_max = img->p.smax / 2;
+    int grid = 0;
+    size_t smem = 0;
+    st = finish_params(lp, t, &grid, &smem);
+    if (st != HD_OK) return st;
+    if (cudaMemsetAsync(base, 0, L.control_bytes, s) != cudaSuccess) return HD_ERR_CUDA;
+    if (launch_table_upload(base + L.desc_off, tab.data(), tab.size(), (void *)s) != 0) return HD_ERR_CUDA;
+    if (launch_persistent(lp, grid, smem, (void *)s) != 0) return HD_ERR_CUDA;
+
+    // the Wiener filter of the whole median image
+    hd_image fi = *img;
+    fi.src = fbuf;
+    fi.src_pitch = f_pitch;
+    const int mode = img->p.noise_var < 0.0 ? MODE_WIENER_EST : MODE_WIENER_GIVEN;
+    return run_single(&fi, mode, base + L.wiener_off, L.desc_off - L.wiener_off, s);
 }
 
 hd_status hybrid_batched_workspace_size(const hd_image *imgs, int n, size_t *bytes)
