@@ -201,6 +201,22 @@ __device__ __forceinline__ void warp_find(const u32 *hist, u32 wb0, u32 wb1, u32
     }
 }
 
+// Index of the first of four bins whose cumulative count, from `pre`, reaches T.
+__device__ __forceinline__ u32 first_reaching(const u32 (&c4)[4], u32 pre, u32 T)
+{
+    u32 c = pre, idx = 3;
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c += c4[j];
+        if (!found && c >= T) {
+            idx = (u32)j;
+            found = true;
+        }
+    }
+    return idx;
+}
+
 template <int ES>
 __global__ void __launch_bounds__(kCsThreads, 1) contrast_kernel(CsParams p)
 {
@@ -296,27 +312,114 @@ __global__ void __launch_bounds__(kCsThreads, 1) contrast_kernel(CsParams p)
     }
     __syncthreads();
     if (s_ok) {
-        const u32 wb0 = (u32)((u64)warp * p.nbins / kCsWarps), wb1 = (u32)((u64)(warp + 1) * p.nbins / kCsWarps);
-        u32 sum = 0;
-        for (u32 b = wb0 + lane; b < wb1; b += 32) sum += __ldcg(p.hist + b);
-        sum = __reduce_add_sync(kFull, sum);
-        if (lane == 0) s_wsum[warp] = sum;
-        __syncthreads();
-        u32 pre = 0;
-        for (u32 w = 0; w < warp; ++w) pre += s_wsum[w];
-        if (pre < p.t_lo && p.t_lo <= pre + sum) warp_find(p.hist, wb0, wb1, pre, p.t_lo, lane, &s_lo);
-        if (pre < p.t_hi && p.t_hi <= pre + sum) warp_find(p.hist, wb0, wb1, pre, p.t_hi, lane, &s_hi);
+        if (p.nbins <= 4u * kCsThreads) {
+            // four bins a thread, one coalesced read, block prefix sums
+            const u32 b4 = 4u * tid;
+            u32 c4[4] = {0u, 0u, 0u, 0u};
+            if (b4 < p.nbins) {
+                const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p.hist) + tid);
+                c4[0] = v.x;
+                c4[1] = b4 + 1 < p.nbins ? v.y : 0u;
+                c4[2] = b4 + 2 < p.nbins ? v.z : 0u;
+                c4[3] = b4 + 3 < p.nbins ? v.w : 0u;
+            }
+            const u32 cnt = c4[0] + c4[1] + c4[2] + c4[3];
+            u32 incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (u32)o) incl += t;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                u32 t = s_wsum[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 u = __shfl_up_sync(kFull, t, o);
+                    if (lane >= (u32)o) t += u;
+                }
+                s_wsum[lane] = t;
+            }
+            __syncthreads();
+            const u32 pre = (warp ? s_wsum[warp - 1] : 0u) + incl - cnt;   // pixels in bins below b4
+            if (pre < p.t_lo && p.t_lo <= pre + cnt) s_lo = b4 + first_reaching(c4, pre, p.t_lo);
+            if (pre < p.t_hi && p.t_hi <= pre + cnt) s_hi = b4 + first_reaching(c4, pre, p.t_hi);
+        } else {
+            // 13..16 bits: each warp sums its range, then rescans the range
+            // that holds the limit
+            const u32 wb0 = (u32)((u64)warp * p.nbins / kCsWarps), wb1 = (u32)((u64)(warp + 1) * p.nbins / kCsWarps);
+            u32 sum = 0;
+            for (u32 b = wb0 + lane; b < wb1; b += 32) sum += __ldcg(p.hist + b);
+            sum = __reduce_add_sync(kFull, sum);
+            if (lane == 0) s_wsum[warp] = sum;
+            __syncthreads();
+            u32 pre = 0;
+            for (u32 w = 0; w < warp; ++w) pre += s_wsum[w];
+            if (pre < p.t_lo && p.t_lo <= pre + sum) warp_find(p.hist, wb0, wb1, pre, p.t_lo, lane, &s_lo);
+            if (pre < p.t_hi && p.t_hi <= pre + sum) warp_find(p.hist, wb0, wb1, pre, p.t_hi, lane, &s_hi);
+        }
     }
     __syncthreads();
+    // count this CTA out of the histogram; the result is needed only at the
+    // end, so the round trip overlaps the remap
+    u32 old_scanned = 0;
     if (tid == 0) {
         __threadfence();
-        const u32 old = atomicAdd(&p.ctl->scanned, 1u);
+        old_scanned = atomicAdd(&p.ctl->scanned, 1u);
+    }
+
+    // ---- pass C: remap the share (nothing to do after a timeout, or for the
+    // identity in place)
+    const u32 lo = s_lo, hi = s_hi;
+    if (s_ok && !(lo == hi && p.src == p.dst && p.sp == p.dp)) {
+        const float scale = lo < hi ? __fdiv_rn((float)p.maxv, (float)(hi - lo)) : 0.0f;
+        if (p.shared) {
+            for (u32 v = tid; v < p.nbins; v += kCsThreads) lut[v] = (uint16_t)(lo < hi ? stretch_px(v, lo, hi, p.maxv, scale) : v);
+            __syncthreads();
+        }
+        auto map = [&](u32 x) -> u32 {
+            if (p.shared) return lut[min(x, p.maxv)];
+            return lo < hi ? stretch_px(x, lo, hi, p.maxv, scale) : x;
+        };
+        if (p.flat) {
+            const FlatSplit f = flat_split<ES>(p, b0, b1);
+            if (tid < f.head) store_px<ES>(p.dst, b0 + tid, map(load_px<ES>(p.src, b0 + tid)));
+            if (tid < f.tail) store_px<ES>(p.dst, b1 - f.tail + tid, map(load_px<ES>(p.src, b1 - f.tail + tid)));
+            const uint4 *vs = reinterpret_cast<const uint4 *>(p.src + (size_t)(b0 + f.head) * ES);
+            uint4 *vd = reinterpret_cast<uint4 *>(p.dst + (size_t)(b0 + f.head) * ES);
+            for (u32 c0 = tid; c0 < f.nvec; c0 += 4 * kCsThreads) {
+                uint4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const u32 c = c0 + u * kCsThreads;
+                    if (c < f.nvec) v[u] = vs[c];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const u32 c = c0 + u * kCsThreads;
+                    if (c >= f.nvec) break;
+                    u32 px[V];
+                    unpack<ES>(v[u], px);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) px[i] = map(px[i]);
+                    vd[c] = pack<ES>(px);
+                }
+            }
+        } else {
+            for_pieces(p, ES, b0, b1, [&](const uint8_t *srow, uint8_t *drow, u32 n) {
+                for (u32 j = tid; j < n; j += kCsThreads) store_px<ES>(drow, j, map(load_px<ES>(srow, j)));
+            });
+        }
+    }
+
+    // the last CTA out of the histogram clears it and the counters
+    if (tid == 0) {
         __threadfence();
-        s_last = old == gridDim.x - 1;
+        s_last = old_scanned == gridDim.x - 1;
     }
     __syncthreads();
     if (s_last) {
-        // every CTA has read the histogram: clear it and the counters
         for (u32 b = tid; b < p.nbins; b += kCsThreads) p.hist[b] = 0;
         __syncthreads();
         if (tid == 0) {
@@ -324,49 +427,6 @@ __global__ void __launch_bounds__(kCsThreads, 1) contrast_kernel(CsParams p)
             p.ctl->scanned = 0;
             __threadfence();
         }
-    }
-    if (!s_ok) return;
-
-    // ---- pass C: remap the share
-    const u32 lo = s_lo, hi = s_hi;
-    if (lo == hi && p.src == p.dst && p.sp == p.dp) return;   // identity in place
-    const float scale = lo < hi ? __fdiv_rn((float)p.maxv, (float)(hi - lo)) : 0.0f;
-    if (p.shared) {
-        for (u32 v = tid; v < p.nbins; v += kCsThreads) lut[v] = (uint16_t)(lo < hi ? stretch_px(v, lo, hi, p.maxv, scale) : v);
-        __syncthreads();
-    }
-    auto map = [&](u32 x) -> u32 {
-        if (p.shared) return lut[min(x, p.maxv)];
-        return lo < hi ? stretch_px(x, lo, hi, p.maxv, scale) : x;
-    };
-    if (p.flat) {
-        const FlatSplit f = flat_split<ES>(p, b0, b1);
-        if (tid < f.head) store_px<ES>(p.dst, b0 + tid, map(load_px<ES>(p.src, b0 + tid)));
-        if (tid < f.tail) store_px<ES>(p.dst, b1 - f.tail + tid, map(load_px<ES>(p.src, b1 - f.tail + tid)));
-        const uint4 *vs = reinterpret_cast<const uint4 *>(p.src + (size_t)(b0 + f.head) * ES);
-        uint4 *vd = reinterpret_cast<uint4 *>(p.dst + (size_t)(b0 + f.head) * ES);
-        for (u32 c0 = tid; c0 < f.nvec; c0 += 4 * kCsThreads) {
-            uint4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const u32 c = c0 + u * kCsThreads;
-                if (c < f.nvec) v[u] = vs[c];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const u32 c = c0 + u * kCsThreads;
-                if (c >= f.nvec) break;
-                u32 px[V];
-                unpack<ES>(v[u], px);
-#pragma unroll
-                for (int i = 0; i < V; ++i) px[i] = map(px[i]);
-                vd[c] = pack<ES>(px);
-            }
-        }
-    } else {
-        for_pieces(p, ES, b0, b1, [&](const uint8_t *srow, uint8_t *drow, u32 n) {
-            for (u32 j = tid; j < n; j += kCsThreads) store_px<ES>(drow, j, map(load_px<ES>(srow, j)));
-        });
     }
 }
 
