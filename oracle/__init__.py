@@ -21,6 +21,8 @@ What each function follows in the paper:
                      and each strip is median-filtered alone, its borders
                      reflected at the strip's own edges; the Wiener filter then
                      runs on the whole reassembled image.
+* ``reference_noise_variance`` - Algorithm 1, step 4d with the original
+                     image passed to the Wiener stage: nu2 = mean (f - ref)^2.
 * ``contrast``     - Algorithm 1, step 4e (the paper gives no rule): linear
                      stretch between the k-th smallest and k-th largest
                      values, k = floor(tol * N), exact integer rounding.
@@ -80,6 +82,8 @@ def _load():
             lib.oracle_wiener_stats.restype = I
             lib.oracle_amf_pixel.argtypes = [P, L, L, I, I, L, L]
             lib.oracle_amf_pixel.restype = I
+            lib.oracle_reference_noise_var.argtypes = [P, P, L, P, P]
+            lib.oracle_reference_noise_var.restype = I
             lib.oracle_contrast.argtypes = [P, L, I, ctypes.c_double, P, P]
             lib.oracle_contrast.restype = I
             lib.oracle_check_smax.argtypes = [I]
@@ -244,3 +248,20 @@ def contrast(x: np.ndarray, tol: float = 0.01, bits: int | None = None):
     if rc != ORACLE_OK:
         raise OracleError(rc, "oracle_contrast")
     return out.astype(x.dtype), int(lohi[0]), int(lohi[1])
+
+
+def reference_noise_variance(f: np.ndarray, ref: np.ndarray):
+    """Noise variance of ``f`` against a clean reference image (Algorithm 1,
+    step 4d, where the original image reaches the Wiener stage): the mean of
+    (f - ref)^2 over all pixels, summed exactly, one binary64 division.
+    Returns (nu2, exact sum)."""
+    lib = _load()
+    f16, r16 = _as_u16(f), _as_u16(ref)
+    if f16.shape != r16.shape:
+        raise ValueError("f and ref must have the same shape")
+    nu2 = ctypes.c_double()
+    tot = np.zeros(1, dtype=np.uint64)
+    rc = lib.oracle_reference_noise_var(_ptr(f16), _ptr(r16), f16.size, ctypes.byref(nu2), _ptr(tot))
+    if rc != ORACLE_OK:
+        raise OracleError(rc, "oracle_reference_noise_var")
+    return nu2.value, int(tot[0])

@@ -358,3 +358,22 @@ int oracle_contrast(const uint16_t *x, long N, int bits, double tol, uint16_t *o
     }
     return ORACLE_OK;
 }
+
+/*
+ * Noise variance from a clean reference (Algorithm 1, step 4d passes the
+ * original image to the Wiener stage; the reading is that it supplies the
+ * noise variance): nu2 = mean over pixels of (f - ref)^2, the sum an exact
+ * integer, then fl64(fl64(sum) / N).  sum_out (optional) receives the sum.
+ */
+int oracle_reference_noise_var(const uint16_t *f, const uint16_t *ref, long N, double *nu2, uint64_t *sum_out)
+{
+    if (!f || !ref || !nu2 || N < 1) return ORACLE_ERR_ARG;
+    uint64_t s = 0;
+    for (long i = 0; i < N; ++i) {
+        const int64_t d = (int64_t)f[i] - (int64_t)ref[i];
+        s += (uint64_t)(d * d);
+    }
+    *nu2 = (double)s / (double)N;
+    if (sum_out) *sum_out = s;
+    return ORACLE_OK;
+}

@@ -17,6 +17,10 @@ Partitioned median (Algorithm 1, step 6 with `parts` strips):
   * every strip equals the brute-force median of that strip alone,
   * one part is the whole-image median; rows whose Smax window stays inside
     their strip equal the whole-image median rows.
+Noise variance from a clean reference (Algorithm 1, step 4d):
+  * closed forms: a constant offset c gives c^2, a +-d checkerboard d^2,
+  * the exact sum against numpy's int64 sum, and the division's rounding,
+  * the largest sum that can occur (every pixel 65535 apart) stays exact.
 Contrast stretch (Algorithm 1, step 4e; the rule is a reading, the paper
 gives none):
   * hand-derived worked examples (tests/golden/contrast_worked_examples.json),
@@ -364,6 +368,36 @@ def test_strips_locality(parts):
     np.testing.assert_array_equal(f[inner], whole[inner])
     if parts > 1:
         assert (f != whole).any()          # the seams do change some pixels
+
+
+# --------------------------------------------------------------------------- reference noise variance
+def test_reference_noise_variance_closed_forms():
+    rng = np.random.default_rng(3)
+    r = rng.integers(0, 200, size=(37, 53)).astype(np.uint8)
+    for c in (0, 1, 7, 55):
+        nu2, tot = oracle.reference_noise_variance((r + c).astype(np.uint8), r)
+        assert nu2 == float(c * c) and tot == c * c * r.size
+    d = 9
+    sign = np.where((np.indices(r.shape).sum(axis=0) % 2) == 0, 1, -1)
+    f = (r.astype(np.int64) + 20 + d * sign).astype(np.uint8)
+    nu2, _ = oracle.reference_noise_variance(f, (r + 20).astype(np.uint8))
+    assert nu2 == float(d * d)
+
+
+def test_reference_noise_variance_exact_sum_and_rounding():
+    rng = np.random.default_rng(4)
+    for shape, hi in (((1, 1), 256), ((7, 9), 4096), ((300, 301), 65536)):
+        f = rng.integers(0, hi, size=shape).astype(np.uint16)
+        r = rng.integers(0, hi, size=shape).astype(np.uint16)
+        nu2, tot = oracle.reference_noise_variance(f, r)
+        want = int(((f.astype(np.int64) - r.astype(np.int64)) ** 2).sum())
+        assert tot == want
+        q = Fraction(want) if want < 2 ** 53 else Fraction(float(want))
+        assert nu2 == float(q / f.size)          # fl(fl(sum) / N)
+    # the largest possible sum: 65535^2 a pixel over many pixels stays exact
+    f = np.full((1000, 1000), 65535, np.uint16)
+    nu2, tot = oracle.reference_noise_variance(f, np.zeros_like(f))
+    assert tot == 65535 ** 2 * 10 ** 6 and nu2 == float(65535 ** 2)
 
 
 # --------------------------------------------------------------------------- contrast stretch
