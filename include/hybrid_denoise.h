@@ -194,6 +194,23 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
 #define HD_STATIC_SCRATCH_BYTES (36u * 1024u * 1024u)
 hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
 
+/* ---------------------------------------------------------------- reference
+ * Noise variance of an image against a clean reference (Algorithm 1, step 4d
+ * hands the original image to the Wiener stage; this reads it as the source
+ * of the noise variance):
+ *   nu2 = fl64(fl64(S) / (H W)),  S = sum over pixels of (f - ref)^2, exact.
+ * Pass the result as hd_params.noise_var: the hybrid is then one fused pass.
+ *   f, ref: device images, H x W, row pitches in bytes (>= W * element size),
+ *           same dtype; they may overlap (both are only read).
+ *   nu2_out: device pointer, 8-byte aligned; written when the launch ends.
+ *   workspace: device, 256-byte aligned, >= HD_REFNOISE_WORKSPACE_BYTES,
+ *           zero-filled before first use; each call leaves it zeroed.
+ * One kernel launch; no device-side waits. */
+#define HD_REFNOISE_WORKSPACE_BYTES 256u
+hd_status reference_noise_variance(const void *f, size_t f_pitch, const void *ref, size_t ref_pitch, int H,
+                                   int W, int dtype, double *nu2_out, void *workspace, size_t ws_bytes,
+                                   hd_stream_t stream);
+
 /* ---------------------------------------------------------------- contrast
  * Contrast stretch, the post-processing step of the hybrid (Algorithm 1,
  * step 4e).  The paper gives no rule; this is a linear stretch between two

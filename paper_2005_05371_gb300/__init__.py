@@ -37,7 +37,7 @@ EXPORTS = [
     "hybrid_batched_workspace_size", "hd_batch_plan_create", "hd_batch_plan_launch",
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
     "hd_status_str", "hd_version", "contrast_stretch", "contrast_workspace_size",
-    "hybrid_denoise_strips", "hybrid_strips_workspace_size",
+    "hybrid_denoise_strips", "hybrid_strips_workspace_size", "reference_noise_variance",
 ]
 
 
@@ -91,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "hd_get_device_error": ([P], I),
         "contrast_stretch": ([img_p, ctypes.c_double, P, S, P], I),
         "hybrid_denoise_strips": ([img_p, I, P, S, P], I),
+        "reference_noise_variance": ([P, S, P, S, I, I, I, P, P, S, P], I),
         "hybrid_strips_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
         "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
@@ -271,6 +272,28 @@ def hybrid_denoise_strips(src, dst, parts: int, smax: int = 11, wiener_w: int = 
     _check(_lib.hybrid_denoise_strips(ctypes.byref(img), int(parts), _ws_ptr(workspace), _ws_len(workspace),
                                       _stream_ptr(stream)), "hybrid_denoise_strips")
     return dst
+
+
+HD_REFNOISE_WORKSPACE_BYTES = 256
+
+
+def reference_noise_variance(f, ref, out=None, workspace=None, stream=None):
+    """Noise variance of ``f`` against the clean reference ``ref`` (Algorithm 1,
+    step 4d): mean of (f - ref)^2, exact sum, one binary64 division.  Returns a
+    one-element float64 CUDA tensor (``out`` if given)."""
+    torch = _torch()
+    if f.shape != ref.shape or f.dtype != ref.dtype:
+        raise ValueError("f and ref must have the same shape and dtype")
+    code = _dtype_code(f)
+    H, W = f.shape
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=f.device)
+    if workspace is None:
+        workspace = _workspace(HD_REFNOISE_WORKSPACE_BYTES, f.device)
+    _check(_lib.reference_noise_variance(f.data_ptr(), _pitch(f), ref.data_ptr(), _pitch(ref), H, W, code,
+                                         out.data_ptr(), _ws_ptr(workspace), _ws_len(workspace),
+                                         _stream_ptr(stream)), "reference_noise_variance")
+    return out
 
 
 def contrast_workspace_size(H: int, W: int, dtype_code: int, bits: int | None = None) -> int:
