@@ -141,6 +141,36 @@ hd_status hybrid_denoise(const hd_image *img, void *workspace, size_t ws_bytes,
 hd_status hybrid_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
+/* A host pipeline: many images of one size and one parameter set, from host
+ * buffers to host buffers, with the copies of each step overlapping the
+ * kernels of the steps before and after it.  It holds `depth` slots of device
+ * images (noisy in, result out) in the caller's workspace and three CUDA
+ * streams of its own (copies in, kernels, copies out); step i uses slot
+ * i mod depth, and events make a slot wait for its previous step.
+ *   depth: 1..HD_PIPELINE_DEPTH_MAX (2 overlaps one step's copies with its
+ *          neighbours' kernels).
+ *   workspace: device, 256-byte aligned, >= hd_host_pipeline_workspace_size(),
+ *          zero-filled before first use; owned by the caller, must outlive the
+ *          pipeline.
+ *   submit: src and dst are HOST pointers with row pitches in bytes (pinned
+ *          memory for overlap; pageable memory works without it).  The call
+ *          only enqueues: src must stay unchanged and dst unread until
+ *          hd_host_pipeline_wait returns.  Same filtering, parameters and
+ *          output as hybrid_denoise.
+ *   wait: blocks until every submitted step has finished; HD_ERR_CUDA if a
+ *          stream failed (device-side timeouts: hd_get_device_error).
+ *   destroy: waits, then frees the streams and events (not the workspace). */
+#define HD_PIPELINE_DEPTH_MAX 8
+typedef struct hd_host_pipeline hd_host_pipeline;
+hd_status hd_host_pipeline_workspace_size(int H, int W, int dtype, const hd_params *p, int depth,
+                                          size_t *bytes);
+hd_status hd_host_pipeline_create(int H, int W, int dtype, const hd_params *p, int depth,
+                                  void *workspace, size_t ws_bytes, hd_host_pipeline **pipeline);
+hd_status hd_host_pipeline_submit(hd_host_pipeline *pipeline, const void *src, size_t src_pitch,
+                                  void *dst, size_t dst_pitch);
+hd_status hd_host_pipeline_wait(hd_host_pipeline *pipeline);
+hd_status hd_host_pipeline_destroy(hd_host_pipeline *pipeline);
+
 /* The hybrid with the listing's partitioned median (Algorithm 1, step 6:
  * parallelAdapMedian(g, Smax, parts)).  The image is cut into `parts` row
  * strips, strip i covering rows floor(i H / parts) .. floor((i+1) H / parts) - 1,

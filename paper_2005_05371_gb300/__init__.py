@@ -38,6 +38,8 @@ EXPORTS = [
     "hd_batch_plan_destroy", "hd_set_tuning", "hd_get_tuning", "hd_set_spin_limit", "hd_get_device_error",
     "hd_status_str", "hd_version", "contrast_stretch", "contrast_workspace_size",
     "hybrid_denoise_strips", "hybrid_strips_workspace_size", "reference_noise_variance",
+    "hd_host_pipeline_workspace_size", "hd_host_pipeline_create", "hd_host_pipeline_submit",
+    "hd_host_pipeline_wait", "hd_host_pipeline_destroy",
 ]
 
 
@@ -92,6 +94,11 @@ def _load() -> ctypes.CDLL:
         "contrast_stretch": ([img_p, ctypes.c_double, P, S, P], I),
         "hybrid_denoise_strips": ([img_p, I, P, S, P], I),
         "reference_noise_variance": ([P, S, P, S, I, I, I, P, P, S, P], I),
+        "hd_host_pipeline_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
+        "hd_host_pipeline_create": ([I, I, I, par_p, I, P, S, ctypes.POINTER(P)], I),
+        "hd_host_pipeline_submit": ([P, P, S, P, S], I),
+        "hd_host_pipeline_wait": ([P], I),
+        "hd_host_pipeline_destroy": ([P], I),
         "hybrid_strips_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
         "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
@@ -352,6 +359,58 @@ def hybrid_denoise_host(src: np.ndarray, dst: np.ndarray, smax: int = 11, wiener
     _check(_lib.hybrid_denoise_host(ctypes.byref(img), _ws_ptr(workspace), _ws_len(workspace),
                                     _stream_ptr(stream)), "hybrid_denoise_host")
     return dst
+
+
+def _host_ptr_pitch(a):
+    """(pointer, row pitch, dtype code, shape) of a host image: numpy array or CPU tensor."""
+    if isinstance(a, np.ndarray):
+        if a.ndim != 2 or a.strides[1] != a.itemsize:
+            raise ValueError("host image rows must be contiguous")
+        return a.ctypes.data, a.strides[0], (HD_U8 if a.dtype == np.uint8 else HD_U16), a.shape
+    return a.data_ptr(), _pitch(a), _dtype_code(a), tuple(a.shape)
+
+
+class HostPipeline:
+    """Host-to-host hybrid of many images of one size (hd_host_pipeline_*):
+    the copies of each step overlap the kernels of its neighbours.  ``submit``
+    only enqueues; results are valid after ``wait``."""
+
+    def __init__(self, H: int, W: int, dtype_code: int, params: Params, depth: int = 2, device="cuda"):
+        self.H, self.W, self.code = H, W, dtype_code
+        c = params.to_c(dtype_code)
+        n = ctypes.c_size_t()
+        _check(_lib.hd_host_pipeline_workspace_size(H, W, dtype_code, ctypes.byref(c), depth, ctypes.byref(n)),
+               "hd_host_pipeline_workspace_size")
+        self.workspace = _workspace(n.value, device)
+        h = ctypes.c_void_p()
+        _check(_lib.hd_host_pipeline_create(H, W, dtype_code, ctypes.byref(c), depth, _ws_ptr(self.workspace),
+                                            _ws_len(self.workspace), ctypes.byref(h)), "hd_host_pipeline_create")
+        self._h = h
+        self._pending = []
+
+    def submit(self, src, dst):
+        sp, spitch, code, shape = _host_ptr_pitch(src)
+        dp, dpitch, code2, shape2 = _host_ptr_pitch(dst)
+        if code != self.code or code2 != self.code or tuple(shape) != (self.H, self.W) or tuple(shape2) != (self.H, self.W):
+            raise ValueError("images must match the pipeline's size and dtype")
+        self._pending.append((src, dst))          # keep the host buffers alive until wait()
+        _check(_lib.hd_host_pipeline_submit(self._h, sp, spitch, dp, dpitch), "hd_host_pipeline_submit")
+
+    def wait(self):
+        _check(_lib.hd_host_pipeline_wait(self._h), "hd_host_pipeline_wait")
+        self._pending.clear()
+
+    def close(self):
+        if self._h:
+            _lib.hd_host_pipeline_destroy(self._h)
+            self._h = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hybrid_denoise_static(src, dst, smax: int = 11, wiener_w: int = 5, noise_var: float = -1.0,

@@ -405,6 +405,23 @@ size_t hybrid_min_bytes(const void *img_)
 }
 }  // namespace hd
 
+// A host pipeline keeps `depth` slots of device images (noisy in, result out)
+// in the caller's workspace and three streams: host-to-device copies, kernels,
+// device-to-host copies.  Step i uses slot i mod depth; events order the
+// reuse of a slot after its previous step, so the copies of one step overlap
+// the kernels of its neighbours.
+struct hd_host_pipeline {
+    int H = 0, W = 0, dtype = 0;
+    hd_params p{};
+    int depth = 0;
+    uint8_t *ws = nullptr;
+    size_t core = 0;          // bytes of the hybrid workspace at the start
+    size_t plane = 0;         // bytes of one device image
+    cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_k, ev_out;
+    long long submitted = 0;
+};
+
 struct hd_batch_plan {
     void *ws = nullptr;
     LaunchParams lp;
@@ -587,6 +604,145 @@ hd_status hybrid_denoise_strips(const hd_image *img, int parts, void *workspace,
     fi.src_pitch = f_pitch;
     const int mode = img->p.noise_var < 0.0 ? MODE_WIENER_EST : MODE_WIENER_GIVEN;
     return run_single(&fi, mode, base + L.wiener_off, L.desc_off - L.wiener_off, s);
+}
+
+static size_t pipeline_plane(int H, int W, int dtype)
+{
+    return round_up((size_t)H * (size_t)W * elem_size(dtype), kAlign);
+}
+
+hd_status hd_host_pipeline_workspace_size(int H, int W, int dtype, const hd_params *p, int depth, size_t *bytes)
+{
+    if (!bytes || depth < 1 || depth > HD_PIPELINE_DEPTH_MAX) return HD_ERR_ARG;
+    size_t b = 0;
+    hd_status st = hybrid_workspace_size(H, W, dtype, p, &b);
+    if (st != HD_OK) return st;
+    *bytes = round_up(b, kAlign) + 2 * (size_t)depth * pipeline_plane(H, W, dtype);
+    return HD_OK;
+}
+
+static void pipeline_release(hd_host_pipeline *pl)
+{
+    if (pl->comp) cudaStreamSynchronize(pl->comp);
+    if (pl->h2d) cudaStreamSynchronize(pl->h2d);
+    if (pl->d2h) cudaStreamSynchronize(pl->d2h);
+    for (auto *v : {&pl->ev_in, &pl->ev_k, &pl->ev_out})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {pl->h2d, pl->comp, pl->d2h})
+        if (st) cudaStreamDestroy(st);
+    delete pl;
+}
+
+hd_status hd_host_pipeline_create(int H, int W, int dtype, const hd_params *p, int depth, void *workspace,
+                                  size_t ws_bytes, hd_host_pipeline **out)
+{
+    if (!out || !p) return HD_ERR_ARG;
+    *out = nullptr;
+    size_t need = 0;
+    hd_status st = hd_host_pipeline_workspace_size(H, W, dtype, p, depth, &need);
+    if (st != HD_OK) return st;
+    if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < need) return HD_ERR_WORKSPACE;
+    hd_host_pipeline *pl = new (std::nothrow) hd_host_pipeline();
+    if (!pl) return HD_ERR_ARG;
+    pl->H = H;
+    pl->W = W;
+    pl->dtype = dtype;
+    pl->p = *p;
+    pl->depth = depth;
+    pl->ws = static_cast<uint8_t *>(workspace);
+    size_t core = 0;
+    hybrid_workspace_size(H, W, dtype, p, &core);
+    pl->core = round_up(core, kAlign);
+    pl->plane = pipeline_plane(H, W, dtype);
+    // the parameters are checked once, on slot 0's images
+    hd_image img;
+    std::memset(&img, 0, sizeof(img));
+    img.src = pl->ws + pl->core;
+    img.dst = pl->ws + pl->core + pl->plane;
+    img.H = H;
+    img.W = W;
+    img.src_pitch = img.dst_pitch = (size_t)W * elem_size(dtype);
+    img.dtype = dtype;
+    img.p = *p;
+    st = check_image(&img, true, true, false);
+    if (st != HD_OK) {
+        delete pl;
+        return st;
+    }
+    bool ok = true;
+    for (cudaStream_t *sp : {&pl->h2d, &pl->comp, &pl->d2h})
+        ok = ok && cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto *v : {&pl->ev_in, &pl->ev_k, &pl->ev_out}) {
+        v->assign(depth, nullptr);
+        for (cudaEvent_t &e : *v) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        pipeline_release(pl);
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
+    *out = pl;
+    return HD_OK;
+}
+
+hd_status hd_host_pipeline_submit(hd_host_pipeline *pl, const void *src, size_t src_pitch, void *dst,
+                                  size_t dst_pitch)
+{
+    if (!pl || !src || !dst) return HD_ERR_ARG;
+    const size_t row = (size_t)pl->W * elem_size(pl->dtype);
+    if (src_pitch < row || dst_pitch < row) return HD_ERR_ARG;
+    const int s = (int)(pl->submitted % pl->depth);
+    uint8_t *dsrc = pl->ws + pl->core + 2 * (size_t)s * pl->plane;
+    uint8_t *ddst = dsrc + pl->plane;
+    const size_t H = (size_t)pl->H;
+    // in: after the slot's previous kernel has read its noisy image
+    if (cudaStreamWaitEvent(pl->h2d, pl->ev_k[s], 0) != cudaSuccess) return HD_ERR_CUDA;
+    const cudaError_t ein = src_pitch == row
+                                ? cudaMemcpyAsync(dsrc, src, row * H, cudaMemcpyHostToDevice, pl->h2d)
+                                : cudaMemcpy2DAsync(dsrc, row, src, src_pitch, row, H, cudaMemcpyHostToDevice,
+                                                    pl->h2d);
+    if (ein != cudaSuccess || cudaEventRecord(pl->ev_in[s], pl->h2d) != cudaSuccess) return HD_ERR_CUDA;
+    // kernel: after the copy in, and after the slot's previous result has left
+    if (cudaStreamWaitEvent(pl->comp, pl->ev_in[s], 0) != cudaSuccess) return HD_ERR_CUDA;
+    if (cudaStreamWaitEvent(pl->comp, pl->ev_out[s], 0) != cudaSuccess) return HD_ERR_CUDA;
+    hd_image img;
+    std::memset(&img, 0, sizeof(img));
+    img.src = dsrc;
+    img.dst = ddst;
+    img.H = pl->H;
+    img.W = pl->W;
+    img.src_pitch = img.dst_pitch = row;
+    img.dtype = pl->dtype;
+    img.p = pl->p;
+    hd_status st = run_single(&img, hybrid_mode(&img), pl->core ? pl->ws : nullptr, pl->core, pl->comp);
+    if (st != HD_OK) return st;
+    if (cudaEventRecord(pl->ev_k[s], pl->comp) != cudaSuccess) return HD_ERR_CUDA;
+    // out: after the kernel
+    if (cudaStreamWaitEvent(pl->d2h, pl->ev_k[s], 0) != cudaSuccess) return HD_ERR_CUDA;
+    const cudaError_t eout = dst_pitch == row
+                                 ? cudaMemcpyAsync(dst, ddst, row * H, cudaMemcpyDeviceToHost, pl->d2h)
+                                 : cudaMemcpy2DAsync(dst, dst_pitch, ddst, row, row, H, cudaMemcpyDeviceToHost,
+                                                     pl->d2h);
+    if (eout != cudaSuccess || cudaEventRecord(pl->ev_out[s], pl->d2h) != cudaSuccess) return HD_ERR_CUDA;
+    ++pl->submitted;
+    return HD_OK;
+}
+
+hd_status hd_host_pipeline_wait(hd_host_pipeline *pl)
+{
+    if (!pl) return HD_ERR_ARG;
+    bool ok = cudaStreamSynchronize(pl->h2d) == cudaSuccess;
+    ok = cudaStreamSynchronize(pl->comp) == cudaSuccess && ok;
+    ok = cudaStreamSynchronize(pl->d2h) == cudaSuccess && ok;
+    return ok ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_host_pipeline_destroy(hd_host_pipeline *pl)
+{
+    if (!pl) return HD_ERR_ARG;
+    pipeline_release(pl);
+    return HD_OK;
 }
 
 hd_status hybrid_batched_workspace_size(const hd_image *imgs, int n, size_t *bytes)
