@@ -131,3 +131,67 @@ def test_batched_validation():
     plan = ctypes.c_void_p()
     assert hd._lib.hd_batch_plan_create(imgs, 2, 0x10000, 1 << 30, ctypes.byref(plan)) == hd.HD_ERR_SMAX
     assert hd._lib.hd_batch_plan_launch(None, None) == hd.HD_ERR_ARG
+
+
+def test_contrast_argument_checks_before_launch():
+    lib = hd._lib
+    img = _img()
+    for tol in (-0.1, 0.5, float("nan")):
+        assert lib.contrast_stretch(ctypes.byref(img), tol, 0x10000, 1 << 20, None) == hd.HD_ERR_ARG
+    # in place is allowed only with the same pitch; partial overlap is refused
+    ov = _img(src=0x100000, dst=0x100004)
+    assert lib.contrast_stretch(ctypes.byref(ov), 0.01, 0x10000, 1 << 20, None) == hd.HD_ERR_ARG
+    assert lib.contrast_stretch(ctypes.byref(img), 0.01, None, 0, None) == hd.HD_ERR_WORKSPACE
+    assert lib.contrast_stretch(ctypes.byref(img), 0.01, 0x10008, 1 << 20, None) == hd.HD_ERR_WORKSPACE
+    need = hd.contrast_workspace_size(16, 16, hd.HD_U8)
+    assert need == 256 + 256 * 4
+    assert lib.contrast_stretch(ctypes.byref(img), 0.01, 0x10000, need - 1, None) == hd.HD_ERR_WORKSPACE
+    assert hd.contrast_workspace_size(16, 16, hd.HD_U16, 12) == 256 + 4096 * 4
+    assert lib.contrast_stretch(ctypes.byref(_img(dtype=hd.HD_U8, bits=12)), 0.01, 0x10000, 1 << 20,
+                                None) == hd.HD_ERR_DTYPE
+
+
+def test_strips_argument_checks_before_launch():
+    lib = hd._lib
+    img = _img(H=16)
+    for parts in (0, -2, 17):
+        assert lib.hybrid_denoise_strips(ctypes.byref(img), parts, 0x10000, 1 << 30, None) == hd.HD_ERR_ARG
+    assert lib.hybrid_denoise_strips(ctypes.byref(_img(smax=4)), 2, 0x10000, 1 << 30, None) == hd.HD_ERR_SMAX
+    p = hd.Params(7, 5)
+    # one part is the whole-image hybrid; more parts add the strip tables
+    assert hd.hybrid_strips_workspace_size(64, 64, hd.HD_U8, p, 1) == hd.hybrid_workspace_size(64, 64, hd.HD_U8, p)
+    assert hd.hybrid_strips_workspace_size(64, 64, hd.HD_U8, p, 8) > hd.hybrid_strips_workspace_size(64, 64, hd.HD_U8, p, 2)
+    need = hd.hybrid_strips_workspace_size(16, 16, hd.HD_U8, hd.Params(5, 3), 4)
+    assert lib.hybrid_denoise_strips(ctypes.byref(img), 4, 0x10000, need - 1, None) == hd.HD_ERR_WORKSPACE
+
+
+def test_reference_and_pipeline_argument_checks():
+    lib = hd._lib
+    S = ctypes.c_size_t
+    assert lib.reference_noise_variance(None, 16, 0x2000, 16, 16, 16, hd.HD_U8, 0x3000, 0x10000, 256,
+                                        None) == hd.HD_ERR_ARG
+    assert lib.reference_noise_variance(0x1000, 15, 0x2000, 16, 16, 16, hd.HD_U8, 0x3000, 0x10000, 256,
+                                        None) == hd.HD_ERR_ARG
+    assert lib.reference_noise_variance(0x1000, 16, 0x2000, 16, 16, 16, hd.HD_U8, 0x3004, 0x10000, 256,
+                                        None) == hd.HD_ERR_ARG                       # misaligned output
+    assert lib.reference_noise_variance(0x1000, 16, 0x2000, 16, 16, 16, hd.HD_U8, 0x3000, 0x10000, 255,
+                                        None) == hd.HD_ERR_WORKSPACE
+    assert lib.reference_noise_variance(0x1000, 32, 0x2001, 32, 16, 16, hd.HD_U16, 0x3000, 0x10000, 256,
+                                        None) == hd.HD_ERR_ARG                       # odd u16 address
+    n = S()
+    c = hd.Params(7, 5).to_c(hd.HD_U8)
+    for depth in (0, 9):
+        assert lib.hd_host_pipeline_workspace_size(64, 64, hd.HD_U8, ctypes.byref(c), depth,
+                                                   ctypes.byref(n)) == hd.HD_ERR_ARG
+    assert lib.hd_host_pipeline_workspace_size(64, 64, hd.HD_U8, ctypes.byref(c), 2, ctypes.byref(n)) == hd.HD_OK
+    core = hd.hybrid_workspace_size(64, 64, hd.HD_U8, hd.Params(7, 5))
+    assert n.value == (core + 255) // 256 * 256 + 2 * 2 * ((64 * 64 + 255) // 256 * 256)
+    pl = ctypes.c_void_p()
+    bad = hd.Params(8, 5).to_c(hd.HD_U8)
+    assert lib.hd_host_pipeline_create(64, 64, hd.HD_U8, ctypes.byref(bad), 2, 0x10000, 1 << 30,
+                                       ctypes.byref(pl)) == hd.HD_ERR_SMAX
+    assert lib.hd_host_pipeline_create(64, 64, hd.HD_U8, ctypes.byref(c), 2, 0x10000, n.value - 1,
+                                       ctypes.byref(pl)) == hd.HD_ERR_WORKSPACE
+    assert lib.hd_host_pipeline_submit(None, 0x1000, 64, 0x2000, 64) == hd.HD_ERR_ARG
+    assert lib.hd_host_pipeline_wait(None) == hd.HD_ERR_ARG
+    assert lib.hd_host_pipeline_destroy(None) == hd.HD_ERR_ARG
