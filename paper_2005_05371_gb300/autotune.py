@@ -2,9 +2,10 @@
 
 The tunables are the rows per work item (`region_h`: the median/Wiener region
 is 64 columns x region_h rows) and the grid size in CTAs per SM.  `sweep`
-times every candidate on seeded images of each size class with CUDA events
-over CUDA-graph replays; `tune` keeps the fastest per class and writes a JSON
-table; `choose` / `apply` pick the entry for an image at call time.  Results
+times every candidate on seeded images of each size class, and on a batch
+plan of uneven slices, with CUDA events over CUDA-graph replays; `tune` keeps
+the fastest per class and writes a JSON table; `choose` / `apply` pick the
+entry for an image at call time and `choose_batch` the one for batches.  Results
 never depend on the tuning (the tests check several shapes), only the speed.
 """
 from __future__ import annotations
@@ -65,9 +66,31 @@ def time_config(hd, torch, spec, g, region_h, ctas, steps=20, warmup=3):
     return e0.elapsed_time(e1) / steps
 
 
+def time_batch(hd, torch, items, region_h, ctas, launches=10):
+    """Mean ms per launch of a batch plan for one tuning."""
+    hd.hd_set_tuning(region_h, ctas)
+    plan = hd.BatchPlan(items)
+    s = torch.cuda.Stream()
+    try:
+        for _ in range(3):
+            plan.launch(s)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            for _ in range(launches):
+                plan.launch(s)
+            e1.record(s)
+        s.synchronize()
+        return e0.elapsed_time(e1) / launches
+    finally:
+        plan.close()
+
+
 def sweep():
     import torch
     import paper_2005_05371_gb300 as hd
+    import synth
     old = hd.hd_get_tuning()
     out = {}
     try:
@@ -79,6 +102,15 @@ def sweep():
                         ms = time_config(hd, torch, spec, g, rh, c)
                         out.setdefault(cls, []).append({"region_h": rh, "ctas_per_sm": c, "ms": ms,
                                                         "H": spec.H, "W": spec.W})
+        # batches: 64 uneven 12-bit slices of the batched workload's kind
+        items = []
+        for sp in synth.batch_specs(64, master_seed=400):
+            src = torch.from_numpy(sp.noisy().view(np.int16)).cuda()
+            items.append((src, torch.empty_like(src), hd.Params(sp.smax, sp.wiener_w, -1.0, 0, 0, sp.bits)))
+        for rh in REGION_H:
+            for c in CTAS_PER_SM:
+                out.setdefault("batch", []).append({"region_h": rh, "ctas_per_sm": c,
+                                                    "ms": time_batch(hd, torch, items, rh, c), "images": 64})
     finally:
         hd.hd_set_tuning(*old)
     return out
@@ -109,6 +141,15 @@ def choose(H: int, W: int, path: str = TABLE_PATH):
     ent = _loaded.get(size_class(H, W))
     if not ent:
         return 32, 0
+    return int(ent["region_h"]), int(ent["ctas_per_sm"])
+
+
+def choose_batch(path: str = TABLE_PATH):
+    """(region_h, ctas_per_sm) for batched launches (default: the large-image entry)."""
+    choose(1, 1, path)
+    ent = _loaded.get("batch")
+    if not ent:
+        return choose(4096, 4096, path)
     return int(ent["region_h"]), int(ent["ctas_per_sm"])
 
 
