@@ -622,7 +622,8 @@ def main():
             raise SystemExit(f"device error in the per-kernel timing: {hd.hd_status_str(status)}")
     achieved = step_bytes / (hybrid_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload),
+                "frac": round(achieved / peak, 4),
+                "traffic": recorded_traffic(args.workload) if args.parts == 1 else None,
                 "kernel": "hd_persistent_kernel", "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": step_bytes}
