@@ -51,6 +51,12 @@ sys.path.insert(0, ROOT)
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "hybrid AMF+Wiener Mpixel/s on 1 GB300 (batched vs plain); p50/p99 served latency"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+# algorithmic operations per pixel: 3x3 level A/B with shared column sorts
+# (about 20 min/max and 6 compare/select) and the Wiener stage (about 10
+# integer and 10 FP32 operations); window growth is not counted
+OPS_PER_PIXEL = 46
+ALU_LANES_PER_SM = 128          # 32-bit INT/FP32 lanes of one SM (4 partitions x 32)
+SM_MAX_GHZ = 2.07
 
 
 # --------------------------------------------------------------------------- helpers
@@ -621,12 +627,24 @@ def main():
         if status != hd.HD_OK:
             raise SystemExit(f"device error in the per-kernel timing: {hd.hd_status_str(status)}")
     achieved = step_bytes / (hybrid_ms / 1e3) / 1e9
+    # the integer/FP32 side of the roofline: algorithmic operations per pixel
+    # of the 3x3 median stage and the Wiener stage (window growth not
+    # counted, so this is a lower bound of the work) against the SMs' 32-bit
+    # lanes at the maximum SM clock
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * ALU_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    alu_achieved = px_per_step * OPS_PER_PIXEL / (hybrid_ms / 1e3) / 1e12
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": recorded_traffic(args.workload) if args.parts == 1 else None,
                 "kernel": "hd_persistent_kernel", "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": step_bytes}
+    roofline_alu = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2),
+                    "unit": "Tops/s", "frac": round(alu_achieved / alu_peak, 4),
+                    "ops_per_pixel": OPS_PER_PIXEL, "kernel": "hd_persistent_kernel",
+                    "peak_kind": f"derived: {props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x "
+                                 f"{SM_MAX_GHZ} GHz"}
 
     if plain_step is not None:
         plain_ms, _, _ = timed(plain_step, max(3, args.steps // 5), args.warmup, False)
@@ -740,7 +758,8 @@ def main():
             "config": {**cfg, "parallelism": f"replicas x{world}",
                        "l2": f"inputs rotate over {copies} device copies ({copies * step_bytes / 2**20:.0f} MiB "
                              f"of algorithmic traffic > 129 MB L2)"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks, **extra,
         }
         print(json.dumps(line), flush=True)
