@@ -8,8 +8,8 @@
 //   out = x where lo == hi, else
 //   out = floor((clamp(x, lo, hi) - lo) * maxv / (hi - lo) + 1/2)   (exact integers).
 //
-// One launch of a grid of one 1024-thread CTA per SM at most, all resident
-// at once (checked with the occupancy query).  Every CTA owns a fixed 1/gridDim share of the pixels in
+// One cooperative launch of a grid of one 1024-thread CTA per SM at most (all
+// resident at once; the occupancy query sizes it).  Every CTA owns a fixed 1/gridDim share of the pixels in
 // row-major order and makes three passes over it:
 //   A  histogram of the share.  Up to 12 bits it lives in shared memory in R
 //      interleaved copies (R = 32 for 8 bits, 2 for 12; lane l adds to copy
@@ -553,9 +553,24 @@ hd_status contrast_stretch(const hd_image *img, double tol, void *workspace, siz
     if (per_sm < 1 || sms < 1) return HD_ERR_CUDA;
     const u32 by_size = (p.N + kCsMinPxPerCta - 1) / kCsMinPxPerCta;
     const int grid = (int)std::max(1u, std::min(by_size, (u32)(sms * per_sm)));
-    if (es == 1) contrast_kernel<1><<<grid, kCsThreads, smem, (cudaStream_t)stream>>>(p);
-    else contrast_kernel<2><<<grid, kCsThreads, smem, (cudaStream_t)stream>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return HD_ERR_CUDA;
+    // a cooperative launch: the CTAs wait for one another, so they must all be
+    // resident at once (the bounded wait stays as a safety net)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kCsThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = es == 1 ? cudaLaunchKernelEx(&cfg, contrast_kernel<1>, p)
+                                  : cudaLaunchKernelEx(&cfg, contrast_kernel<2>, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
     return HD_OK;
 }
 
