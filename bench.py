@@ -347,8 +347,11 @@ def run_served(args, rank, world, dev, hd, torch):
             reqs = []
             t0 = time.perf_counter()
             for i, t in enumerate(arrivals):
-                while time.perf_counter() - t0 < t:
-                    pass
+                # sleep to the arrival time: a busy wait would hold the
+                # interpreter lock that the scheduler thread needs
+                wait = t - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
                 j = i % len(hosts)
                 reqs.append(srv.submit(hosts[j], params_of(j), outs[j]))
             for r in reqs:

@@ -288,13 +288,16 @@ def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
 
 
 def replay(server: Server, pool, arrivals, params_of, want_results: bool = False):
-    """Submit pool images at the given arrival offsets (busy-wait pacing)."""
+    """Submit pool images at the given arrival offsets (paced by sleeping)."""
     torch = server.torch
     t0 = time.perf_counter()
     reqs = []
     for i, t in enumerate(arrivals):
-        while time.perf_counter() - t0 < t:
-            pass
+        # sleep to the arrival time: a busy wait would hold the interpreter
+        # lock that the scheduler thread needs
+        wait = t - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
         host = pool[i % len(pool)]
         out = torch.empty_like(host).pin_memory() if want_results else None
         reqs.append(server.submit(host, params_of(i), out))
