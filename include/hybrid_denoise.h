@@ -159,7 +159,9 @@ hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p,
  *          output as hybrid_denoise.
  *   wait: blocks until every submitted step has finished; HD_ERR_CUDA if a
  *          stream failed (device-side timeouts: hd_get_device_error).
- *   destroy: waits, then frees the streams and events (not the workspace). */
+ *   destroy: waits, then frees the streams and events (not the workspace).
+ * One pipeline is used by one host thread at a time (its calls are not
+ * synchronised with each other); separate pipelines are independent. */
 #define HD_PIPELINE_DEPTH_MAX 8
 typedef struct hd_host_pipeline hd_host_pipeline;
 hd_status hd_host_pipeline_workspace_size(int H, int W, int dtype, const hd_params *p, int depth,
@@ -178,7 +180,8 @@ hd_status hd_host_pipeline_destroy(hd_host_pipeline *pipeline);
  * reflect at the strip's edges, so pixels within Smax/2 rows of a seam can
  * differ from hybrid_denoise.  The Wiener filter then runs on the whole
  * reassembled median image.  parts = 1 is exactly hybrid_denoise.
- *   parts: 1..H, else HD_ERR_ARG.
+ *   parts: 1..H, else HD_ERR_ARG.  Each strip costs one descriptor (about
+ *   150 bytes) written into the workspace by small launches of 30 KB each.
  *   workspace: device, 256-byte aligned, >= hybrid_strips_workspace_size()
  *   bytes.  Each call clears the counters it uses first (a memset on the
  *   stream), so one workspace serves calls of any size and partition in turn.
