@@ -56,6 +56,21 @@ def test_pipeline_matches_oracle(depth, dtype, bits):
     pl.close()
 
 
+def test_pipeline_with_given_noise_variance():
+    """A supplied noise variance: the hybrid needs no workspace of its own, so
+    the slots start at the front of the pipeline's workspace."""
+    H, W = 97, 133
+    imgs = [noisy_image(H, W, np.uint8, seed=300 + i) for i in range(5)]
+    pl = hd.HostPipeline(H, W, hd.HD_U8, hd.Params(7, 3, noise_var=40.0), depth=2)
+    outs = [np.zeros_like(g) for g in imgs]
+    for g, o in zip(imgs, outs):
+        pl.submit(g, o)
+    pl.wait()
+    pl.close()
+    for g, o in zip(imgs, outs):
+        np.testing.assert_array_equal(o, oracle.hybrid(g, 7, 3, noise_var=40.0)[1].out32)
+
+
 def test_pipeline_argument_errors():
     pl = hd.HostPipeline(40, 50, hd.HD_U8, hd.Params(7, 3), depth=2)
     with pytest.raises(ValueError):
