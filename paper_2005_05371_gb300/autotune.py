@@ -127,18 +127,23 @@ def tune(path: str = TABLE_PATH):
     return table
 
 
-_loaded = None
+_loaded: dict = {}
+
+
+def _table(path: str) -> dict:
+    """The tuned table at `path` (read once per path; {} if there is none)."""
+    if path not in _loaded:
+        tab = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                tab = json.load(fh).get("table", {})
+        _loaded[path] = tab
+    return _loaded[path]
 
 
 def choose(H: int, W: int, path: str = TABLE_PATH):
     """(region_h, ctas_per_sm) for an image, from the tuned table (default (32, 0))."""
-    global _loaded
-    if _loaded is None:
-        _loaded = {}
-        if os.path.exists(path):
-            with open(path) as fh:
-                _loaded = json.load(fh).get("table", {})
-    ent = _loaded.get(size_class(H, W))
+    ent = _table(path).get(size_class(H, W))
     if not ent:
         return 32, 0
     return int(ent["region_h"]), int(ent["ctas_per_sm"])
@@ -146,8 +151,7 @@ def choose(H: int, W: int, path: str = TABLE_PATH):
 
 def choose_batch(path: str = TABLE_PATH):
     """(region_h, ctas_per_sm) for batched launches (default: the large-image entry)."""
-    choose(1, 1, path)
-    ent = _loaded.get("batch")
+    ent = _table(path).get("batch")
     if not ent:
         return choose(4096, 4096, path)
     return int(ent["region_h"]), int(ent["ctas_per_sm"])
