@@ -124,7 +124,8 @@ hd_status wiener_filter(const hd_image *img, void *workspace, size_t ws_bytes,
                         hd_stream_t stream);
 hd_status wiener_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
-/* The hybrid (Algorithm 1, step 4, without the contrast stretch of step 4e):
+/* The hybrid (Algorithm 1, step 4, without the contrast stretch of step 4e,
+ * which is contrast_stretch below):
  * dst = Wiener(AdaptiveMedian(src)).  One persistent kernel launch: the
  * median output stays in the workspace (L2-resident for images up to tens of
  * MB); with a caller-supplied noise_var >= 0 the whole hybrid is one pass and
@@ -143,7 +144,9 @@ hd_status hybrid_min_workspace_size(int H, int W, int dtype, const hd_params *p,
 
 /* A host pipeline: many images of one size and one parameter set, from host
  * buffers to host buffers, with the copies of each step overlapping the
- * kernels of the steps before and after it.  It holds `depth` slots of device
+ * kernels of the steps before and after it.  Each step is the hybrid of
+ * Algorithm 1, step 4; the pipelining has no counterpart in the paper (its
+ * images are single files on one CPU).  It holds `depth` slots of device
  * images (noisy in, result out) in the caller's workspace and three CUDA
  * streams of its own (copies in, kernels, copies out); step i uses slot
  * i mod depth, and events make a slot wait for its previous step.
@@ -271,7 +274,8 @@ hd_status contrast_stretch(const hd_image *img, double tol, void *workspace, siz
 hd_status contrast_workspace_size(int H, int W, int dtype, const hd_params *p, size_t *bytes);
 
 /* ---------------------------------------------------------------- batches
- * Many images of uneven sizes and per-image parameters in ONE persistent
+ * Many images of uneven sizes and per-image parameters (each the hybrid of
+ * Algorithm 1, step 4; the paper runs one image at a time) in ONE persistent
  * kernel launch: a device work queue of (image, phase, tile) items where an
  * image's Wiener tiles start as soon as that image's median tiles are done,
  * so one image's Wiener overlaps another's median.  Each result is
