@@ -199,11 +199,18 @@ def build_workload(name: str, rank: int):
     if name == "batched":
         specs = synth.batch_specs(256, master_seed=400 + rank)
         return [(s, s.noisy()) for s in specs]
+    if name == "served":
+        return served_pool(seed=501 + rank)
     raise SystemExit(f"unknown workload {name}")
 
 
 def describe(name: str, items, stretch: float | None = None, parts: int = 1) -> dict:
     px = sum(s.H * s.W for s, _ in items)
+    if name == "served":
+        return {"workload": "served: pool of 16 seeded phantoms, side log-uniform [512, 4096], u8 / 12-bit "
+                            "50/50, s&p up to 0.3, Smax {5..11}, Wiener {3,5,7} (the reference arm denoises "
+                            "the pool's images one after another)", "images": len(items),
+                "megapixels": round(px / 1e6, 3)}
     if name == "batched":
         return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
                             "density U[0.01,0.5], Smax {5,7,9,11}, Wiener {3,5,7}, one persistent launch "
@@ -288,7 +295,8 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * px_step / value, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8" if items[0][0].dtype == "u8" else "u16", "data": "synthetic",
+        "vs_baseline": None, "data": "synthetic",
+        "dtype": "u8+u16" if args.workload == "served" else ("u8" if items[0][0].dtype == "u8" else "u16"),
         "config": describe(args.workload, items, args.stretch, args.parts),
         "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
                          "sample": f"per step ~{per_step:.1f} s of the C oracle (single thread) on {descr}"},

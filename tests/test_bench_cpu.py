@@ -22,7 +22,8 @@ def _reference_line(*extra):
 
 
 @pytest.mark.parametrize("extra", [(), ("--workload", "plain512", "--stretch", "0.01"),
-                                   ("--workload", "plain512", "--parts", "4")])
+                                   ("--workload", "plain512", "--parts", "4"), ("--workload", "batched"),
+                                   ("--workload", "served")])
 def test_reference_arm_line(extra):
     d = _reference_line(*extra)
     assert d["impl"] == "reference" and d["unit"] == "Mpixel/s" and d["value"] > 0
