@@ -228,6 +228,27 @@ def describe(name: str, items, stretch: float | None = None, parts: int = 1) -> 
     return d
 
 
+def quality(outs, cleans, noisies, bits) -> dict:
+    """PSNR (dB) and max abs error of the denoised images against the clean
+    phantoms, beside the same figures for the noisy inputs (all images pooled)."""
+    maxv = float((1 << bits) - 1)
+
+    def stats(imgs):
+        se, n, mx = 0.0, 0, 0
+        for a, c in zip(imgs, cleans):
+            d = a.astype(np.int64) - c.astype(np.int64)
+            se += float((d * d).sum())
+            n += d.size
+            mx = max(mx, int(np.abs(d).max()))
+        mse = se / n
+        return (round(10.0 * math.log10(maxv * maxv / mse), 3) if mse > 0 else float("inf")), mx
+
+    p_out, m_out = stats(outs)
+    p_in, m_in = stats(noisies)
+    return {"psnr_db": p_out, "max_abs_error": m_out, "noisy_psnr_db": p_in, "noisy_max_abs_error": m_in,
+            "against": "the clean synthetic phantom", "images": len(outs)}
+
+
 def algorithmic_bytes(items) -> int:
     """Read the noisy input once and write the result once."""
     return sum(2 * s.H * s.W * (1 if s.dtype == "u8" else 2) for s, _ in items)
@@ -760,6 +781,22 @@ def main():
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                "api": "one copy in + hd_batch_plan_launch + one copy out a step (pinned host buffers, "
                       "two buffer sets on two streams)"}
+
+    # output quality against the clean phantoms, from one more step outside the
+    # timed region (the hybrid output, before any contrast stretch)
+    def host_image(t, spec):
+        a = t.cpu().numpy()
+        return a.view(np.uint16) if spec.dtype != "u8" else a
+    if args.workload == "batched":
+        plans[0].launch(stream)
+        torch.cuda.synchronize(dev)
+        outs = [host_image(dst, spec) for (_, dst, _), (spec, _) in zip(bufs[0], items)]
+        extra["quality"] = quality(outs, [spec.clean() for spec, _ in items], [g for _, g in items], 12)
+    else:
+        hybrid_step(0, stream)
+        torch.cuda.synchronize(dev)
+        spec0, g0 = items[0]
+        extra["quality"] = quality([host_image(dsts[0], spec0)], [spec0.clean()], [g0], spec0.bits)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -47,3 +47,24 @@ def test_describe_and_algorithmic_bytes():
     assert bench.algorithmic_bytes(items) == 2 * 1620 * 1620
     s4 = synth.CONFIGS["stress4096"]
     assert bench.algorithmic_bytes([(s4, None)]) == 4 * 4096 * 4096
+
+
+def test_quality_psnr_and_max_error():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    c = np.full((10, 10), 100, np.uint8)
+    o = c.copy()
+    o[0, 0] = 110                                    # one error of 10: MSE = 100 / 100 = 1
+    n = c.copy()
+    n[:] = 120                                       # MSE 400
+    q = bench.quality([o], [c], [n], 8)
+    assert q["max_abs_error"] == 10 and q["noisy_max_abs_error"] == 20
+    assert q["psnr_db"] == round(10 * np.log10(255.0 ** 2 / 1.0), 3)
+    assert q["noisy_psnr_db"] == round(10 * np.log10(255.0 ** 2 / 400.0), 3)
+    assert bench.quality([c], [c], [n], 8)["psnr_db"] == float("inf")
+    # pooled over images of different sizes, 12-bit scale
+    a, b = np.zeros((2, 2), np.uint16), np.zeros((1, 4), np.uint16)
+    a2, b2 = a + 1, b + 3                            # squared errors 4 x 1 and 4 x 9: MSE 5
+    q = bench.quality([a2, b2], [a, b], [a2, b2], 12)
+    assert q["psnr_db"] == round(10 * np.log10(4095.0 ** 2 / 5.0), 3) and q["max_abs_error"] == 3
