@@ -195,3 +195,26 @@ def test_reference_and_pipeline_argument_checks():
     assert lib.hd_host_pipeline_submit(None, 0x1000, 64, 0x2000, 64) == hd.HD_ERR_ARG
     assert lib.hd_host_pipeline_wait(None) == hd.HD_ERR_ARG
     assert lib.hd_host_pipeline_destroy(None) == hd.HD_ERR_ARG
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """The ABI header compiles as C99 (no C++ in its declarations) and a C
+    program that takes the address of every entry point links against the
+    library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = declared_functions()
+    src = tmp_path / "use_abi.c"
+    src.write_text('#include "hybrid_denoise.h"\n#include <stdio.h>\nint main(void) {\n'
+                   + "".join(f'    printf("%p\\n", (void *)&{n});\n' for n in names)
+                   + '    return hd_version() > 0 ? 0 : 1;\n}\n')
+    exe = tmp_path / "use_abi"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src),
+                        "-o", str(exe), os.path.join(root, "paper_2005_05371_gb300", "libhd.so"),
+                        "-Wl,-rpath," + os.path.join(root, "paper_2005_05371_gb300")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
