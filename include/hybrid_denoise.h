@@ -221,12 +221,15 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
  *   - Every GPU that loads the library holds the array until the process
  *     exits.
  *   - The first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture.
+ *     (with that device current), and so does the first call after the
+ *     device's context was destroyed and created again (cudaDeviceReset);
+ *     make those calls before any stream capture.
  *   - All calls on a device share the one array: calls that overlap in time
  *     on the GPU race and corrupt each other's results.  The array keeps the
  *     last call's contents; each call clears the queue counters it needs.
- * Same filtering, parameters, errors and output as hybrid_denoise. */
+ * Same filtering, parameters and output as hybrid_denoise, and the same
+ * argument errors in the same order; HD_ERR_OVERFLOW for a size beyond the
+ * array comes after them. */
 #define HD_STATIC_SCRATCH_BYTES (36u * 1024u * 1024u)
 hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
 
@@ -299,6 +302,38 @@ hd_status hd_batch_plan_create(const hd_image *imgs, int n, void *workspace, siz
                                hd_batch_plan **plan);
 hd_status hd_batch_plan_launch(hd_batch_plan *plan, hd_stream_t stream);
 hd_status hd_batch_plan_destroy(hd_batch_plan *plan);
+
+/* A batch pipeline: the same batch (sizes, dtypes and parameters fixed at
+ * creation) run again and again from host buffers to host buffers, each step
+ * the batched hybrid above (Algorithm 1, step 4 for every image; the
+ * pipelining has no counterpart in the paper).  It holds `depth` slots, each
+ * with device planes for every image (noisy in, result out, tight rows) and a
+ * batch plan over them, and three CUDA streams of its own (copies in, kernels,
+ * copies out); step i uses slot i mod depth and events make a slot wait for
+ * its previous step, so one step's copies overlap its neighbours' kernels.
+ *   imgs, n: the batch; only H, W, dtype and p of each image are used (src,
+ *          dst, noise_var_out and y_out are ignored and may be null).
+ *   depth: 1..HD_PIPELINE_DEPTH_MAX.
+ *   workspace: device, 256-byte aligned, >= hd_batch_pipeline_workspace_size(),
+ *          owned by the caller, must outlive the pipeline.  Creation writes the
+ *          plans' tables into it (synchronous copies).
+ *   submit: srcs[i] / dsts[i] are HOST pointers to image i with row pitches in
+ *          bytes (pinned memory for overlap).  Images whose rows are tight and
+ *          that follow each other in host memory, as they do in the slot,
+ *          move as one copy.  The call only enqueues: srcs must stay unchanged
+ *          and dsts unread until hd_batch_pipeline_wait returns.
+ *   wait: blocks until every submitted step has finished; HD_ERR_CUDA if a
+ *          stream failed (device-side timeouts: hd_get_device_error).
+ *   destroy: waits, then frees the plans, streams and events.
+ * One pipeline is used by one host thread at a time. */
+typedef struct hd_batch_pipeline hd_batch_pipeline;
+hd_status hd_batch_pipeline_workspace_size(const hd_image *imgs, int n, int depth, size_t *bytes);
+hd_status hd_batch_pipeline_create(const hd_image *imgs, int n, int depth, void *workspace, size_t ws_bytes,
+                                   hd_batch_pipeline **pipeline);
+hd_status hd_batch_pipeline_submit(hd_batch_pipeline *pipeline, const void *const *srcs,
+                                   const size_t *src_pitches, void *const *dsts, const size_t *dst_pitches);
+hd_status hd_batch_pipeline_wait(hd_batch_pipeline *pipeline);
+hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pipeline);
 
 /* ---------------------------------------------------------------- tuning
  * Work-item shape of the persistent kernel.  Each item covers a region of

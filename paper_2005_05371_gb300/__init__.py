@@ -40,6 +40,8 @@ EXPORTS = [
     "hybrid_denoise_strips", "hybrid_strips_workspace_size", "reference_noise_variance",
     "hd_host_pipeline_workspace_size", "hd_host_pipeline_create", "hd_host_pipeline_submit",
     "hd_host_pipeline_wait", "hd_host_pipeline_destroy",
+    "hd_batch_pipeline_workspace_size", "hd_batch_pipeline_create", "hd_batch_pipeline_submit",
+    "hd_batch_pipeline_wait", "hd_batch_pipeline_destroy",
 ]
 
 
@@ -99,6 +101,12 @@ def _load() -> ctypes.CDLL:
         "hd_host_pipeline_submit": ([P, P, S, P, S], I),
         "hd_host_pipeline_wait": ([P], I),
         "hd_host_pipeline_destroy": ([P], I),
+        "hd_batch_pipeline_workspace_size": ([img_p, I, I, ctypes.POINTER(S)], I),
+        "hd_batch_pipeline_create": ([img_p, I, I, P, S, ctypes.POINTER(P)], I),
+        "hd_batch_pipeline_submit": ([P, ctypes.POINTER(P), ctypes.POINTER(S), ctypes.POINTER(P),
+                                      ctypes.POINTER(S)], I),
+        "hd_batch_pipeline_wait": ([P], I),
+        "hd_batch_pipeline_destroy": ([P], I),
         "hybrid_strips_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
         "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
@@ -474,6 +482,68 @@ class BatchPlan:
         if self._plan:
             _lib.hd_batch_plan_destroy(self._plan)
             self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _shape_image(H: int, W: int, dtype_code: int, params: Params) -> hd_image:
+    """hd_image carrying only a size, dtype and parameters (no buffers)."""
+    es = 1 if dtype_code == HD_U8 else 2
+    return hd_image(None, None, int(H), int(W), W * es, W * es, dtype_code, params.to_c(dtype_code), None, None)
+
+
+class BatchPipeline:
+    """Host-to-host batched hybrid (hd_batch_pipeline_*): the same batch of
+    uneven images run step after step from host buffers, each step's copies
+    overlapping its neighbours' kernels.  ``shapes`` is a list of
+    (H, W, dtype_code, Params).  ``submit`` only enqueues; results are valid
+    after ``wait``."""
+
+    def __init__(self, shapes, depth: int = 2, device="cuda"):
+        self._arr = (hd_image * len(shapes))()
+        for i, (H, W, code, p) in enumerate(shapes):
+            self._arr[i] = _shape_image(H, W, code, p)
+        self.shapes = [(int(H), int(W), int(code)) for H, W, code, _ in shapes]
+        n = ctypes.c_size_t()
+        _check(_lib.hd_batch_pipeline_workspace_size(self._arr, len(self._arr), depth, ctypes.byref(n)),
+               "hd_batch_pipeline_workspace_size")
+        self.workspace = _workspace(n.value, device)
+        h = ctypes.c_void_p()
+        _check(_lib.hd_batch_pipeline_create(self._arr, len(self._arr), depth, _ws_ptr(self.workspace),
+                                             _ws_len(self.workspace), ctypes.byref(h)), "hd_batch_pipeline_create")
+        self._h = h
+        self._pending = []
+
+    def submit(self, srcs, dsts):
+        """srcs / dsts: host images (numpy arrays or pinned CPU tensors), one per batch image."""
+        n = len(self.shapes)
+        if len(srcs) != n or len(dsts) != n:
+            raise ValueError("one source and one destination per batch image")
+        sp, spi = (ctypes.c_void_p * n)(), (ctypes.c_size_t * n)()
+        dp, dpi = (ctypes.c_void_p * n)(), (ctypes.c_size_t * n)()
+        for i, (a, b) in enumerate(zip(srcs, dsts)):
+            p0, pitch0, c0, sh0 = _host_ptr_pitch(a)
+            p1, pitch1, c1, sh1 = _host_ptr_pitch(b)
+            H, W, code = self.shapes[i]
+            if c0 != code or c1 != code or tuple(sh0) != (H, W) or tuple(sh1) != (H, W):
+                raise ValueError(f"image {i} does not match the pipeline's size and dtype")
+            sp[i], spi[i], dp[i], dpi[i] = p0, pitch0, p1, pitch1
+        self._pending.append((srcs, dsts))        # keep the host buffers alive until wait()
+        _check(_lib.hd_batch_pipeline_submit(self._h, sp, spi, dp, dpi), "hd_batch_pipeline_submit")
+
+    def wait(self):
+        _check(_lib.hd_batch_pipeline_wait(self._h), "hd_batch_pipeline_wait")
+        self._pending.clear()
+
+    def close(self):
+        if self._h:
+            _lib.hd_batch_pipeline_destroy(self._h)
+            self._h = None
+            self._pending.clear()
 
     def __del__(self):
         try:

@@ -396,6 +396,8 @@ int hybrid_on_workspace(const void *img_, void *ws, size_t ws_bytes, void *strea
     return run_single(img, hybrid_mode(img), ws, ws_bytes, (cudaStream_t)stream);
 }
 
+int check_hybrid_image(const void *img) { return check_image(static_cast<const hd_image *>(img), true, true, false); }
+
 size_t hybrid_control_bytes() { return ctl_bytes(); }
 
 size_t hybrid_min_bytes(const void *img_)
@@ -835,6 +837,227 @@ hd_status hd_batch_plan_destroy(hd_batch_plan *plan)
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     delete plan;
+    return HD_OK;
+}
+
+// A batch pipeline keeps `depth` slots, each with device planes for every
+// image of the batch (noisy in, result out) and its own batch plan over them,
+// and three streams as the host pipeline does: step i uses slot i mod depth,
+// and events order a slot's reuse after its previous step.
+struct BatchPipeLayout {
+    std::vector<size_t> off;      // per image: offset of its plane within a slot's plane area
+    std::vector<size_t> bytes;    // per image: H * W * element size (tight rows)
+    size_t planes = 0;            // bytes of one plane area (all images)
+    size_t batch_ws = 0;          // bytes of one slot's batch workspace
+    size_t slot = 0;              // bytes of one slot: [batch workspace][noisy planes][result planes]
+};
+
+static hd_status batch_pipe_layout(const hd_image *imgs, int n, BatchPipeLayout &L)
+{
+    if (!imgs || n < 1) return HD_ERR_ARG;
+    if (n > (1 << 20)) return HD_ERR_OVERFLOW;
+    L.off.resize(n);
+    L.bytes.resize(n);
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        const hd_image &im = imgs[i];
+        if (im.dtype != HD_U8 && im.dtype != HD_U16) return HD_ERR_DTYPE;
+        if (im.H < 1 || im.W < 1) return HD_ERR_ARG;
+        if (im.H > HD_DIM_MAX || im.W > HD_DIM_MAX) return HD_ERR_OVERFLOW;
+        const size_t es = (size_t)elem_size(im.dtype);
+        // planes packed back to back, each aligned to its element size: a batch
+        // of one dtype is one contiguous run (one copy when the host side is too)
+        o = round_up(o, es);
+        L.off[i] = o;
+        L.bytes[i] = (size_t)im.H * (size_t)im.W * es;
+        o += L.bytes[i];
+    }
+    L.planes = round_up(o, kAlign);
+    L.batch_ws = round_up(batch_layout(imgs, n).total, kAlign);
+    L.slot = L.batch_ws + 2 * L.planes;
+    return HD_OK;
+}
+
+struct hd_batch_pipeline {
+    int n = 0, depth = 0;
+    BatchPipeLayout L;
+    std::vector<size_t> row;      // per image: W * element size
+    std::vector<int> H;
+    uint8_t *ws = nullptr;
+    std::vector<hd_batch_plan *> plans;
+    cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_k, ev_out;
+    long long submitted = 0;
+};
+
+static void batch_pipe_release(hd_batch_pipeline *pl)
+{
+    for (cudaStream_t st : {pl->comp, pl->h2d, pl->d2h})
+        if (st) cudaStreamSynchronize(st);
+    for (hd_batch_plan *p : pl->plans)
+        if (p) hd_batch_plan_destroy(p);
+    for (auto *v : {&pl->ev_in, &pl->ev_k, &pl->ev_out})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {pl->h2d, pl->comp, pl->d2h})
+        if (st) cudaStreamDestroy(st);
+    delete pl;
+}
+
+// Copies of one direction for all images of a slot: runs of images whose host
+// rows are tight and whose host and device planes both follow each other
+// without a gap move as one copy; any other image moves on its own.
+static hd_status batch_pipe_copies(const hd_batch_pipeline *pl, uint8_t *dev_area, const void *const *host,
+                                   const size_t *pitch, bool to_device, cudaStream_t s)
+{
+    const int n = pl->n;
+    const uint8_t *run_host = nullptr;
+    uint8_t *run_dev = nullptr;
+    size_t run_len = 0;
+    auto flush = [&]() -> bool {
+        if (!run_len) return true;
+        const cudaError_t e =
+            to_device ? cudaMemcpyAsync(run_dev, run_host, run_len, cudaMemcpyHostToDevice, s)
+                      : cudaMemcpyAsync(const_cast<uint8_t *>(run_host), run_dev, run_len, cudaMemcpyDeviceToHost, s);
+        run_len = 0;
+        return e == cudaSuccess;
+    };
+    for (int i = 0; i < n; ++i) {
+        const uint8_t *h = static_cast<const uint8_t *>(host[i]);
+        uint8_t *d = dev_area + pl->L.off[i];
+        const size_t row = pl->row[i], bytes = pl->L.bytes[i];
+        if (pitch[i] == row) {
+            if (run_len && h == run_host + run_len && d == run_dev + run_len) {
+                run_len += bytes;
+                continue;
+            }
+            if (!flush()) return HD_ERR_CUDA;
+            run_host = h;
+            run_dev = d;
+            run_len = bytes;
+            continue;
+        }
+        if (!flush()) return HD_ERR_CUDA;
+        const cudaError_t e =
+            to_device ? cudaMemcpy2DAsync(d, row, h, pitch[i], row, (size_t)pl->H[i], cudaMemcpyHostToDevice, s)
+                      : cudaMemcpy2DAsync(const_cast<uint8_t *>(h), pitch[i], d, row, row, (size_t)pl->H[i],
+                                          cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return HD_ERR_CUDA;
+    }
+    return flush() ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_batch_pipeline_workspace_size(const hd_image *imgs, int n, int depth, size_t *bytes)
+{
+    if (!bytes || depth < 1 || depth > HD_PIPELINE_DEPTH_MAX) return HD_ERR_ARG;
+    BatchPipeLayout L;
+    hd_status st = batch_pipe_layout(imgs, n, L);
+    if (st != HD_OK) return st;
+    *bytes = (size_t)depth * L.slot;
+    return HD_OK;
+}
+
+hd_status hd_batch_pipeline_create(const hd_image *imgs, int n, int depth, void *workspace, size_t ws_bytes,
+                                   hd_batch_pipeline **out)
+{
+    if (!out) return HD_ERR_ARG;
+    *out = nullptr;
+    size_t need = 0;
+    hd_status st = hd_batch_pipeline_workspace_size(imgs, n, depth, &need);
+    if (st != HD_OK) return st;
+    if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < need) return HD_ERR_WORKSPACE;
+    hd_batch_pipeline *pl = new (std::nothrow) hd_batch_pipeline();
+    if (!pl) return HD_ERR_ARG;
+    pl->n = n;
+    pl->depth = depth;
+    batch_pipe_layout(imgs, n, pl->L);
+    pl->ws = static_cast<uint8_t *>(workspace);
+    pl->row.resize(n);
+    pl->H.resize(n);
+    for (int i = 0; i < n; ++i) {
+        pl->row[i] = (size_t)imgs[i].W * elem_size(imgs[i].dtype);
+        pl->H[i] = imgs[i].H;
+    }
+    // one batch plan per slot over that slot's device planes (the plan checks
+    // every image's parameters)
+    std::vector<hd_image> dimgs(imgs, imgs + n);
+    pl->plans.assign(depth, nullptr);
+    for (int k = 0; k < depth && st == HD_OK; ++k) {
+        uint8_t *slot = pl->ws + (size_t)k * pl->L.slot;
+        uint8_t *in = slot + pl->L.batch_ws, *res = in + pl->L.planes;
+        for (int i = 0; i < n; ++i) {
+            dimgs[i].src = in + pl->L.off[i];
+            dimgs[i].dst = res + pl->L.off[i];
+            dimgs[i].src_pitch = dimgs[i].dst_pitch = pl->row[i];
+            dimgs[i].noise_var_out = nullptr;
+            dimgs[i].y_out = nullptr;
+        }
+        st = hd_batch_plan_create(dimgs.data(), n, slot, pl->L.batch_ws, &pl->plans[k]);
+    }
+    if (st != HD_OK) {
+        batch_pipe_release(pl);
+        return st;
+    }
+    bool ok = true;
+    for (cudaStream_t *sp : {&pl->h2d, &pl->comp, &pl->d2h})
+        ok = ok && cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto *v : {&pl->ev_in, &pl->ev_k, &pl->ev_out}) {
+        v->assign(depth, nullptr);
+        for (cudaEvent_t &e : *v) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        batch_pipe_release(pl);
+        cudaGetLastError();
+        return HD_ERR_CUDA;
+    }
+    *out = pl;
+    return HD_OK;
+}
+
+hd_status hd_batch_pipeline_submit(hd_batch_pipeline *pl, const void *const *srcs, const size_t *src_pitches,
+                                   void *const *dsts, const size_t *dst_pitches)
+{
+    if (!pl || !srcs || !src_pitches || !dsts || !dst_pitches) return HD_ERR_ARG;
+    for (int i = 0; i < pl->n; ++i) {
+        if (!srcs[i] || !dsts[i]) return HD_ERR_ARG;
+        if (src_pitches[i] < pl->row[i] || dst_pitches[i] < pl->row[i]) return HD_ERR_ARG;
+    }
+    const int k = (int)(pl->submitted % pl->depth);
+    uint8_t *slot = pl->ws + (size_t)k * pl->L.slot;
+    uint8_t *in = slot + pl->L.batch_ws, *res = in + pl->L.planes;
+    // in: after the slot's previous kernel has read its noisy planes
+    if (cudaStreamWaitEvent(pl->h2d, pl->ev_k[k], 0) != cudaSuccess) return HD_ERR_CUDA;
+    hd_status st = batch_pipe_copies(pl, in, srcs, src_pitches, true, pl->h2d);
+    if (st != HD_OK) return st;
+    if (cudaEventRecord(pl->ev_in[k], pl->h2d) != cudaSuccess) return HD_ERR_CUDA;
+    // kernel: after the copies in, and after the slot's previous results have left
+    if (cudaStreamWaitEvent(pl->comp, pl->ev_in[k], 0) != cudaSuccess) return HD_ERR_CUDA;
+    if (cudaStreamWaitEvent(pl->comp, pl->ev_out[k], 0) != cudaSuccess) return HD_ERR_CUDA;
+    st = hd_batch_plan_launch(pl->plans[k], pl->comp);
+    if (st != HD_OK) return st;
+    if (cudaEventRecord(pl->ev_k[k], pl->comp) != cudaSuccess) return HD_ERR_CUDA;
+    // out: after the kernel
+    if (cudaStreamWaitEvent(pl->d2h, pl->ev_k[k], 0) != cudaSuccess) return HD_ERR_CUDA;
+    st = batch_pipe_copies(pl, res, const_cast<const void *const *>(dsts), dst_pitches, false, pl->d2h);
+    if (st != HD_OK) return st;
+    if (cudaEventRecord(pl->ev_out[k], pl->d2h) != cudaSuccess) return HD_ERR_CUDA;
+    ++pl->submitted;
+    return HD_OK;
+}
+
+hd_status hd_batch_pipeline_wait(hd_batch_pipeline *pl)
+{
+    if (!pl) return HD_ERR_ARG;
+    bool ok = cudaStreamSynchronize(pl->h2d) == cudaSuccess;
+    ok = cudaStreamSynchronize(pl->comp) == cudaSuccess && ok;
+    ok = cudaStreamSynchronize(pl->d2h) == cudaSuccess && ok;
+    return ok ? HD_OK : HD_ERR_CUDA;
+}
+
+hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pl)
+{
+    if (!pl) return HD_ERR_ARG;
+    batch_pipe_release(pl);
     return HD_OK;
 }
 

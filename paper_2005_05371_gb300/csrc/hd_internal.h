@@ -111,6 +111,9 @@ int sm_count();
 // Device error word helpers.
 int read_and_clear_device_error(unsigned int *out);
 
+// The argument checks of hybrid_denoise, in its order; returns an hd_status value.
+int check_hybrid_image(const void *img);
+
 // hybrid_denoise on a caller-provided workspace (used by the entry point whose
 // scratch is a static device array); returns an hd_status value.
 int hybrid_on_workspace(const void *img, void *ws, size_t ws_bytes, void *stream);

@@ -24,25 +24,69 @@ static __device__ __align__(256) unsigned char g_hd_static_scratch[HD_STATIC_SCR
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_ptr[kMaxDevices];   // device address of the scratch array, per device
+struct Cached {
+    void *ptr;                   // device address of the scratch array
+    unsigned long long ctx_id;   // context it was looked up in (0: unknown)
+};
+Cached g_cache[kMaxDevices];
 
-// The array's name is only a host-side handle in host code: its device
-// address has to be asked for once per device, with that device current.
+// The identity of the calling thread's current context (CUDA driver
+// cuCtxGetCurrent / cuCtxGetId, reached through the runtime's entry-point
+// query so the library needs no link against the driver library).  A
+// context that is destroyed and created again (cudaDeviceReset, then the
+// next runtime call) gets a new identity, and the array may then sit at
+// another address.  Returns false when the identity is not available.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+bool current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!get_cur || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_cur(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0 && *id != 0;
+}
+
+// In host code the array's name is only a host-side handle: its device
+// address has to be asked for with the device current.  The address is
+// looked up on the first call on each device and again whenever the
+// current context is not the one it was looked up in.
 hd_status scratch_address(void **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HD_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return HD_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    Cached &c = g_cache[dev];
+    if (!c.ptr || !have_id || c.ctx_id != id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_hd_static_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return HD_ERR_CUDA;
         }
-        g_ptr[dev] = p;
+        // the lookup itself creates the context when none was current yet
+        unsigned long long id2 = 0;
+        c.ptr = p;
+        c.ctx_id = current_context_id(&id2) ? id2 : 0;
     }
-    *out = g_ptr[dev];
+    *out = c.ptr;
     return HD_OK;
 }
 
@@ -50,11 +94,13 @@ hd_status scratch_address(void **out)
 
 extern "C" hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream)
 {
-    if (!img) return HD_ERR_ARG;
-    if (img->H < 1 || img->W < 1) return HD_ERR_ARG;
+    // the same argument checks, in the same order, as hybrid_denoise; the
+    // size limit of the fixed array comes after them
+    hd_status st = (hd_status)hd::check_hybrid_image(img);
+    if (st != HD_OK) return st;
     size_t need = 0;
     // the smallest workspace is enough; the (mu, s2) plane is used when it fits too
-    hd_status st = hybrid_min_workspace_size(img->H, img->W, img->dtype, &img->p, &need);
+    st = hybrid_min_workspace_size(img->H, img->W, img->dtype, &img->p, &need);
     if (st != HD_OK) return st;
     if (need > HD_STATIC_SCRATCH_BYTES) return HD_ERR_OVERFLOW;
     void *scratch = nullptr;

@@ -197,6 +197,34 @@ def test_reference_and_pipeline_argument_checks():
     assert lib.hd_host_pipeline_destroy(None) == hd.HD_ERR_ARG
 
 
+def test_batch_pipeline_argument_checks():
+    lib = hd._lib
+    S = ctypes.c_size_t
+    shapes = [(64, 64, hd.HD_U16, hd.Params(7, 5, bits=12)), (30, 50, hd.HD_U16, hd.Params(5, 3, bits=12)),
+              (17, 9, hd.HD_U8, hd.Params(9, 7))]
+    arr = (hd.hd_image * 3)(*[hd._shape_image(*s) for s in shapes])
+    n = S()
+    for depth in (0, 9):
+        assert lib.hd_batch_pipeline_workspace_size(arr, 3, depth, ctypes.byref(n)) == hd.HD_ERR_ARG
+    assert lib.hd_batch_pipeline_workspace_size(arr, 0, 2, ctypes.byref(n)) == hd.HD_ERR_ARG
+    assert lib.hd_batch_pipeline_workspace_size(arr, 3, 2, ctypes.byref(n)) == hd.HD_OK
+    # per slot: the batch workspace, then the noisy and result planes packed
+    # back to back (each aligned to its element size)
+    ws = hd.hybrid_batched_workspace_size([hd.hd_image(0x10000, 0x20000000, H, W, W * (1 + c), W * (1 + c), c,
+                                                       p.to_c(c), None, None) for H, W, c, p in shapes])
+    planes = 64 * 64 * 2 + 30 * 50 * 2 + 17 * 9
+    slot = (ws + 255) // 256 * 256 + 2 * ((planes + 255) // 256 * 256)
+    assert n.value == 2 * slot
+    pl = ctypes.c_void_p()
+    assert lib.hd_batch_pipeline_create(arr, 3, 2, 0x10000, n.value - 1, ctypes.byref(pl)) == hd.HD_ERR_WORKSPACE
+    assert lib.hd_batch_pipeline_create(arr, 3, 2, 0x10001, n.value, ctypes.byref(pl)) == hd.HD_ERR_WORKSPACE
+    bad = (hd.hd_image * 1)(hd._shape_image(8, 8, 5, hd.Params(7, 5)))
+    assert lib.hd_batch_pipeline_workspace_size(bad, 1, 2, ctypes.byref(n)) == hd.HD_ERR_DTYPE
+    assert lib.hd_batch_pipeline_submit(None, None, None, None, None) == hd.HD_ERR_ARG
+    assert lib.hd_batch_pipeline_wait(None) == hd.HD_ERR_ARG
+    assert lib.hd_batch_pipeline_destroy(None) == hd.HD_ERR_ARG
+
+
 def test_header_is_plain_c_and_links(tmp_path):
     """The ABI header compiles as C99 (no C++ in its declarations) and a C
     program that takes the address of every entry point links against the

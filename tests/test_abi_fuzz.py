@@ -66,15 +66,32 @@ def draw(rng):
                 dst=dst, border=border, unresolved=unresolved)
 
 
-@pytest.mark.parametrize("fn", ["amf_filter", "wiener_filter", "hybrid_denoise"])
+STATIC_BYTES = 36 * 1024 * 1024
+
+
+def static_min_bytes(H, W, dtype):
+    """hybrid_min_workspace_size with an estimated noise variance: the queue
+    counters and control block (one 256-byte-rounded block) and the median plane
+    with rows padded to 16 bytes."""
+    es = 1 if dtype == hd.HD_U8 else 2
+    ctl = -(-(256 + 64) // 256) * 256
+    return ctl + -(-(H * (-(-W * es // 16) * 16)) // 256) * 256
+
+
+@pytest.mark.parametrize("fn", ["amf_filter", "wiener_filter", "hybrid_denoise", "hybrid_denoise_static"])
 def test_argument_checks_match_the_rules(fn):
-    rng = np.random.default_rng({"amf_filter": 1, "wiener_filter": 2, "hybrid_denoise": 3}[fn])
-    need_amf = fn in ("amf_filter", "hybrid_denoise")
-    need_wiener = fn in ("wiener_filter", "hybrid_denoise")
+    rng = np.random.default_rng({"amf_filter": 1, "wiener_filter": 2, "hybrid_denoise": 3,
+                                 "hybrid_denoise_static": 4}[fn])
+    need_amf = fn in ("amf_filter", "hybrid_denoise", "hybrid_denoise_static")
+    need_wiener = fn in ("wiener_filter", "hybrid_denoise", "hybrid_denoise_static")
     checked = 0
     for _ in range(4000):
         a = draw(rng)
         want = expected(**a, need_amf=need_amf, need_wiener=need_wiener)
+        if want == hd.HD_OK and fn == "hybrid_denoise_static":
+            # after the shared checks: the fixed array's size limit
+            if static_min_bytes(a["H"], a["W"], a["dtype"]) > STATIC_BYTES:
+                want = hd.HD_ERR_OVERFLOW
         if want == hd.HD_OK:
             continue                        # would launch: not sent
         p = hd.hd_params(a["smax"], a["w"], -1.0, a["border"], a["unresolved"], a["bits"])
@@ -82,6 +99,8 @@ def test_argument_checks_match_the_rules(fn):
                           p, None, None)
         if fn == "amf_filter":
             got = hd._lib.amf_filter(ctypes.byref(img), None)
+        elif fn == "hybrid_denoise_static":
+            got = hd._lib.hybrid_denoise_static(ctypes.byref(img), None)
         else:
             got = getattr(hd._lib, fn)(ctypes.byref(img), 0x40000000, 1 << 40, None)
         assert got == want, (fn, a, got, want)
