@@ -2,13 +2,21 @@
 
 Requests (a host image plus filter parameters) arrive at any time.  A
 scheduler thread admits them into a fixed device-memory arena as space
-frees up (admission by a byte budget: input, output and workspace of the
-request), groups every admitted, not yet launched request into one round,
-and launches the round as ONE persistent batched kernel on its own stream.
-Up to `max_inflight` rounds run on the device at once, so requests that
-arrive while others are on the GPU start on the next round without waiting
-for the earlier ones to finish: their work overlaps on the device.  A round's
-completion event marks its requests done; their arena space is then freed.
+frees up, groups every admitted, not yet launched request into one round,
+and launches the round as ONE persistent batched kernel on a stream that no
+running round holds.  Up to `max_inflight` rounds run on the device at once,
+so requests that arrive while others are on the GPU start on the next round
+without waiting for the earlier ones to finish: their work overlaps on the
+device.  A round's completion event marks its requests done; their arena
+space is then freed.
+
+Admission by a byte budget: each admitted request holds ONE arena block with
+its input, its output and the workspace it would need as a batch of its own.
+A round of several requests asks the arena for one workspace for the whole
+round; when no free gap is large enough, the first admitted request runs as
+a round of one inside its own block.  So admission never overcommits the
+arena and the scheduler always makes progress, however fragmented the arena
+is.
 
 Latency of a request = arrival (submit) -> its round's completion event
 observed by the scheduler, including the host->device copy of the input and
@@ -16,6 +24,8 @@ the device->host copy of the result.
 
 Every stage runs in the CUDA library through the C ABI
 (`hybrid_denoise_batched`); this module only schedules, copies and keeps time.
+The device side sits behind a small backend object (`CudaBackend`), so the
+scheduling and the arena can also be exercised without a GPU.
 """
 from __future__ import annotations
 
@@ -27,24 +37,30 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (HD_U8, HD_U16, Params, _check, _lib, _stream_ptr, hd_image, hybrid_batched_workspace_size)
+from . import (HD_U8, HD_U16, Params, _check, _lib, _stream_ptr, hd_image)
 
 ALIGN = 256
 
 
-class DeviceArena:
-    """First-fit allocator over one device buffer of `nbytes` (offsets only;
-    the buffer is a torch tensor owned by the arena)."""
+def _align(n: int) -> int:
+    return (int(n) + ALIGN - 1) // ALIGN * ALIGN
 
-    def __init__(self, nbytes: int, device="cuda:0", buffer=None):
-        import torch
+
+class DeviceArena:
+    """First-fit allocator of offsets into one buffer of `nbytes` (the buffer,
+    if any, is owned by the arena; offsets are multiples of 256)."""
+
+    def __init__(self, nbytes: int, device="cuda:0", buffer=None, allocate: bool = True):
         self.size = int(nbytes) // ALIGN * ALIGN
-        self.buf = buffer if buffer is not None else torch.zeros(self.size, dtype=torch.uint8, device=device)
+        if buffer is None and allocate:
+            import torch
+            buffer = torch.zeros(self.size, dtype=torch.uint8, device=device)
+        self.buf = buffer
         self.free = [(0, self.size)]          # sorted (offset, length)
         self.used = 0
 
     def alloc(self, nbytes: int):
-        n = (int(nbytes) + ALIGN - 1) // ALIGN * ALIGN
+        n = _align(nbytes)
         for i, (off, ln) in enumerate(self.free):
             if ln >= n:
                 if ln == n:
@@ -67,6 +83,9 @@ class DeviceArena:
                 merged.append((o, l))
         self.free = merged
 
+    def largest_gap(self) -> int:
+        return max((l for _, l in self.free), default=0)
+
     def view(self, off: int, nbytes: int):
         return self.buf[off:off + nbytes]
 
@@ -81,35 +100,107 @@ class Request:
     t_done: float = 0.0
     done: threading.Event = field(default_factory=threading.Event)
     error: str | None = None
-    dev: dict = field(default_factory=dict)     # device allocations of this request
+    dev: dict = field(default_factory=dict)     # arena block of this request and the offsets in it
+
+    @property
+    def shape(self) -> tuple[int, int]:
+        return int(self.host.shape[0]), int(self.host.shape[1])
+
+    @property
+    def elem(self) -> int:
+        h = self.host
+        return int(h.element_size()) if hasattr(h, "element_size") else int(h.itemsize)
 
     @property
     def pixels(self) -> int:
-        return int(self.host.shape[0] * self.host.shape[1])
+        H, W = self.shape
+        return H * W
+
+    @property
+    def nbytes(self) -> int:
+        return self.pixels * self.elem
+
+    @property
+    def code(self) -> int:
+        return HD_U8 if self.elem == 1 else HD_U16
 
     @property
     def latency_ms(self) -> float:
         return 1e3 * (self.t_done - self.t_arrive)
 
 
+def _images(reqs, src_dst=None) -> ctypes.Array:
+    """hd_image array for a round; src_dst(i) gives the device pointers (or
+    placeholders for a size query)."""
+    imgs = (hd_image * len(reqs))()
+    for i, r in enumerate(reqs):
+        H, W = r.shape
+        s, d = src_dst(i) if src_dst else (0x1000, 0x1000 + _align(r.nbytes))
+        imgs[i] = hd_image(s, d, H, W, W * r.elem, W * r.elem, r.code, r.params.to_c(r.code), None, None)
+    return imgs
+
+
+class CudaBackend:
+    """The device side of the server: the arena buffer, the streams, and a
+    round = copies in + one hybrid_denoise_batched launch + copies out."""
+
+    def __init__(self, device, n_streams: int):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
+
+    def thread_init(self):
+        self.torch.cuda.set_device(self.device)
+
+    def arena(self, nbytes: int) -> DeviceArena:
+        return DeviceArena(nbytes, self.device)
+
+    @staticmethod
+    def workspace_bytes(reqs) -> int:
+        """hybrid_batched_workspace_size of the requests as one batch (a size
+        query only: no pointer is used)."""
+        imgs = _images(reqs)
+        n = ctypes.c_size_t()
+        _check(_lib.hybrid_batched_workspace_size(imgs, len(reqs), ctypes.byref(n)),
+               "hybrid_batched_workspace_size")
+        return int(n.value)
+
+    def launch(self, arena: DeviceArena, reqs, ws_off: int, ws_len: int, si: int):
+        torch = self.torch
+        s = self.streams[si]
+        base = arena.buf.data_ptr()
+        imgs = _images(reqs, lambda i: (base + reqs[i].dev["src"], base + reqs[i].dev["dst"]))
+        with torch.cuda.stream(s):
+            for r in reqs:
+                arena.view(r.dev["src"], r.nbytes).copy_(r.host.reshape(-1).view(torch.uint8), non_blocking=True)
+        _check(_lib.hybrid_denoise_batched(imgs, len(reqs), base + ws_off, ws_len, _stream_ptr(s)),
+               "hybrid_denoise_batched")
+        with torch.cuda.stream(s):
+            for r in reqs:
+                if r.out is not None:
+                    r.out.reshape(-1).view(torch.uint8).copy_(arena.view(r.dev["dst"], r.nbytes), non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return ev
+
+
 class Server:
     """Continuous batching with admission by a device-memory budget."""
 
     def __init__(self, budget_bytes: int = 8 << 30, max_inflight: int = 3, max_batch: int = 128,
-                 device="cuda:0"):
-        import torch
-        self.torch = torch
-        self.device = torch.device(device)
-        self.arena = DeviceArena(budget_bytes, self.device)
+                 device="cuda:0", backend=None):
+        self.backend = backend if backend is not None else CudaBackend(device, max_inflight)
+        self.arena = self.backend.arena(budget_bytes)
         self.max_inflight = max_inflight
         self.max_batch = max_batch
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(max_inflight)]
         self.lock = threading.Condition()
         self.waiting: deque[Request] = deque()     # arrived, not admitted
         self.admitted: deque[Request] = deque()    # on device, not launched
-        self.inflight: list = []                   # (event, requests, ws_alloc, stream index)
+        self.inflight: list = []                   # (event, requests, round workspace or None, stream index)
         self.finished: list[Request] = []
         self.rounds = 0
+        self.solo_rounds = 0                       # rounds of one run in the request's own block
         self.next_id = 0
         self.stop_flag = False
         self.peak_used = 0
@@ -122,7 +213,8 @@ class Server:
         with self.lock:
             r = Request(self.next_id, host, params, out, time.perf_counter())
             self.next_id += 1
-            if self._request_bytes(r) > self.arena.size:
+            self._layout(r)
+            if r.dev["block"] > self.arena.size:
                 r.error = "request larger than the device-memory budget"
                 r.t_done = time.perf_counter()
                 r.done.set()
@@ -153,93 +245,59 @@ class Server:
         px = sum(r.pixels for r in ok)
         span = (max(r.t_done for r in ok) - min(r.t_arrive for r in ok)) if ok else 1.0
         return {"requests": len(ok), "rejected": len(self.finished) - len(ok), "rounds": self.rounds,
+                "solo_rounds": self.solo_rounds,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mpixel_s": px / span / 1e6, "peak_device_bytes": self.peak_used}
 
     # ------------------------------------------------------------------ scheduler
-    @staticmethod
-    def _img_bytes(r: Request) -> int:
-        return int(r.host.numel() * r.host.element_size())
-
-    def _request_bytes(self, r: Request) -> int:
-        # input + output + this image's share of a batched workspace (median plane, tables)
-        b = self._img_bytes(r)
-        H, W = r.host.shape
-        es = r.host.element_size()
-        return 2 * ((b + ALIGN - 1) // ALIGN * ALIGN) + H * ((W * es + 15) // 16 * 16) + 3 * 1024
+    def _layout(self, r: Request):
+        """Offsets of the request's block: [input][output][own workspace]."""
+        b = _align(r.nbytes)
+        ws1 = _align(self.backend.workspace_bytes([r]))
+        r.dev = {"block": 2 * b + ws1, "src_rel": 0, "dst_rel": b, "ws_rel": 2 * b, "ws_len": ws1}
 
     def _admit(self):
-        # keep room for the workspaces of the requests already admitted
-        reserve = sum(self._request_bytes(r) - 2 * self._img_bytes(r) for r in self.admitted)
+        # first come, first admitted: a request that does not fit waits for
+        # space (the ones behind it wait too, so large requests are not starved)
         while self.waiting:
             r = self.waiting[0]
-            b = self._img_bytes(r)
-            free = self.arena.size - self.arena.used
-            if free - reserve < self._request_bytes(r):
-                return
-            reserve += self._request_bytes(r) - 2 * b
-            a_src = self.arena.alloc(b)
-            if a_src is None:
-                return
-            a_dst = self.arena.alloc(b)
-            if a_dst is None:
-                self.arena.release(*a_src)
+            a = self.arena.alloc(r.dev["block"])
+            if a is None:
                 return
             self.waiting.popleft()
-            r.dev = {"src": a_src, "dst": a_dst}
+            off = a[0]
+            r.dev.update(alloc=a, src=off + r.dev["src_rel"], dst=off + r.dev["dst_rel"], ws=off + r.dev["ws_rel"])
             self.admitted.append(r)
+            self.peak_used = max(self.peak_used, self.arena.used)
 
     def _launch_round(self):
-        """Launch the admitted requests (up to max_batch) as one batched kernel.
-        If the arena has no room for the round's workspace, the round is halved
-        until it fits; returns False when not even one request fits now."""
-        torch = self.torch
+        """Launch admitted requests (up to max_batch) as one batched kernel.
+        A round of several needs a workspace gap in the arena (the round is
+        halved until one fits); otherwise the first request runs alone in its
+        own block."""
         take = min(len(self.admitted), self.max_batch)
-        while take > 0:
+        a_ws = None
+        while take >= 2:
             reqs = [self.admitted[i] for i in range(take)]
-            imgs = (hd_image * take)()
-            for i, r in enumerate(reqs):
-                H, W = r.host.shape
-                es = r.host.element_size()
-                code = HD_U8 if es == 1 else HD_U16
-                src = self.arena.view(r.dev["src"][0], H * W * es)
-                dst = self.arena.view(r.dev["dst"][0], H * W * es)
-                imgs[i] = hd_image(src.data_ptr(), dst.data_ptr(), H, W, W * es, W * es, code,
-                                   r.params.to_c(code), None, None)
-            n = ctypes.c_size_t()
-            _check(_lib.hybrid_batched_workspace_size(imgs, take, ctypes.byref(n)), "hybrid_batched_workspace_size")
-            a_ws = self.arena.alloc(n.value)
+            a_ws = self.arena.alloc(self.backend.workspace_bytes(reqs))
             if a_ws is not None:
                 break
             take //= 2
-        if take == 0:
-            return False
+        if a_ws is None:
+            take = 1
+            reqs = [self.admitted[0]]
+            ws_off, ws_len = reqs[0].dev["ws"], reqs[0].dev["ws_len"]
+            self.solo_rounds += 1
+        else:
+            ws_off, ws_len = a_ws
         for _ in range(take):
             self.admitted.popleft()
-        si = self.rounds % self.max_inflight
-        s = self.streams[si]
-        for r in reqs:
-            H, W = r.host.shape
-            es = r.host.element_size()
-            src = self.arena.view(r.dev["src"][0], H * W * es)
-            with torch.cuda.stream(s):
-                src.copy_(r.host.reshape(-1).view(torch.uint8), non_blocking=True)
-        ws = self.arena.view(a_ws[0], a_ws[1])
-        _check(_lib.hybrid_denoise_batched(imgs, take, ws.data_ptr(), a_ws[1], _stream_ptr(s)),
-               "hybrid_denoise_batched")
-        for r in reqs:
-            if r.out is not None:
-                H, W = r.host.shape
-                es = r.host.element_size()
-                dst = self.arena.view(r.dev["dst"][0], H * W * es)
-                with torch.cuda.stream(s):
-                    r.out.reshape(-1).view(torch.uint8).copy_(dst, non_blocking=True)
-        ev = torch.cuda.Event()
-        ev.record(s)
+        busy = {si for _, _, _, si in self.inflight}
+        si = next(i for i in range(self.max_inflight) if i not in busy)
+        ev = self.backend.launch(self.arena, reqs, ws_off, ws_len, si)
         self.inflight.append((ev, reqs, a_ws, si))
         self.rounds += 1
         self.peak_used = max(self.peak_used, self.arena.used)
-        return True
 
     def _retire(self):
         still = []
@@ -250,10 +308,10 @@ class Server:
                 for r in reqs:
                     r.t_done = t
                     now_done.append(r)
-                self.arena.release(*a_ws)
+                if a_ws is not None:
+                    self.arena.release(*a_ws)
                 for r in reqs:
-                    self.arena.release(*r.dev["src"])
-                    self.arena.release(*r.dev["dst"])
+                    self.arena.release(*r.dev["alloc"])
             else:
                 still.append((ev, reqs, a_ws, si))
         self.inflight = still
@@ -262,15 +320,14 @@ class Server:
             r.done.set()
 
     def _loop(self):
-        torch = self.torch
-        torch.cuda.set_device(self.device)
+        self.backend.thread_init()
         while True:
             with self.lock:
                 if self.stop_flag and not self.waiting and not self.admitted and not self.inflight:
                     return
                 self._retire()
                 self._admit()
-                if self.admitted and len(self.inflight) < self.max_inflight:
+                while self.admitted and len(self.inflight) < self.max_inflight:
                     self._launch_round()
                 idle = not self.admitted and not self.waiting
             if idle and not self.inflight:
@@ -287,9 +344,10 @@ def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
 
 
-def replay(server: Server, pool, arrivals, params_of, want_results: bool = False):
-    """Submit pool images at the given arrival offsets (paced by sleeping)."""
-    torch = server.torch
+def replay(server: Server, pool, arrivals, params_of, want_results: bool = False, outs=None):
+    """Submit pool images at the given arrival offsets (paced by sleeping).
+    Results go to ``outs[i % len(pool)]`` when given, to fresh pinned tensors
+    with ``want_results``, else stay on the device."""
     t0 = time.perf_counter()
     reqs = []
     for i, t in enumerate(arrivals):
@@ -299,6 +357,12 @@ def replay(server: Server, pool, arrivals, params_of, want_results: bool = False
         if wait > 0:
             time.sleep(wait)
         host = pool[i % len(pool)]
-        out = torch.empty_like(host).pin_memory() if want_results else None
+        if outs is not None:
+            out = outs[i % len(pool)]
+        elif want_results:
+            import torch
+            out = torch.empty_like(host).pin_memory()
+        else:
+            out = None
         reqs.append(server.submit(host, params_of(i), out))
     return reqs

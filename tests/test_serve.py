@@ -1,5 +1,7 @@
 """Continuous-batching server: every result in the mix equals the same image
 denoised alone; admission never exceeds the device-memory budget."""
+import time
+
 import numpy as np
 import pytest
 
@@ -23,6 +25,93 @@ def test_arena_first_fit_and_merge():
     a.release(1024, 768)
     a.release(*z)
     assert a.used == 0 and a.free == [(0, 4096)]  # holes merged back
+
+
+class _FakeEvent:
+    def __init__(self, polls):
+        self.polls = polls
+
+    def query(self):
+        self.polls -= 1
+        return self.polls <= 0
+
+
+class _FakeBackend:
+    """The server's device side without a GPU: a round completes after a few
+    polls; every launch checks that the arena regions it uses (each request's
+    block and the round's workspace) overlap no region of a round in flight."""
+
+    def __init__(self, seed):
+        self.rng = np.random.default_rng(seed)
+        self.live = []          # (lo, hi, round id) of regions in flight
+        self.launches = []
+        self.overlaps = 0
+
+    def thread_init(self):
+        pass
+
+    def arena(self, nbytes):
+        from paper_2005_05371_gb300.serve import DeviceArena
+        return DeviceArena(nbytes, allocate=False)
+
+    @staticmethod
+    def workspace_bytes(reqs):
+        # like the batched workspace: tables plus a median plane per image
+        return 4096 + sum(r.shape[0] * ((r.shape[1] * r.elem + 15) // 16 * 16) for r in reqs)
+
+    def launch(self, arena, reqs, ws_off, ws_len, si):
+        rid = len(self.launches)
+        regions = [(r.dev["alloc"][0], r.dev["alloc"][0] + r.dev["alloc"][1]) for r in reqs]
+        own = len(reqs) == 1 and ws_off == reqs[0].dev["ws"]
+        if not own:
+            regions.append((ws_off, ws_off + ws_len))
+        else:
+            assert ws_off + ws_len <= regions[0][1]          # inside the request's own block
+        self.live = [x for x in self.live if not x[3].polls <= 0]
+        for lo, hi in regions:
+            assert 0 <= lo < hi <= arena.size
+            for a, b, _, _ in self.live:
+                if lo < b and a < hi:
+                    self.overlaps += 1
+        ev = _FakeEvent(int(self.rng.integers(1, 6)))
+        self.live += [(lo, hi, rid, ev) for lo, hi in regions]
+        self.launches.append((len(reqs), own, si))
+        return ev
+
+
+def test_scheduler_finishes_every_request_in_a_fragmented_arena():
+    """A small arena and a seeded mix of sizes: requests of every size are
+    admitted and finish, rounds never share arena space, and rounds of one
+    request in its own block keep the scheduler going when no gap can hold a
+    round's workspace (no GPU: the device side is a fake)."""
+    ensure_built()
+    from paper_2005_05371_gb300 import Params
+    from paper_2005_05371_gb300.serve import Server
+    rng = np.random.default_rng(11)
+    fake = _FakeBackend(12)
+    srv = Server(budget_bytes=3 << 20, max_inflight=3, backend=fake)
+    try:
+        reqs = []
+        for i in range(300):
+            H, W = int(rng.integers(8, 700)), int(rng.integers(8, 700))
+            dt = np.uint8 if rng.random() < 0.5 else np.uint16
+            reqs.append(srv.submit(np.zeros((H, W), dt), Params(7, 5, bits=8 if dt == np.uint8 else 12)))
+            if rng.random() < 0.3:
+                time.sleep(0.0005)
+        for r in reqs:
+            assert r.done.wait(30), "a request never finished"
+        st = srv.stats()
+    finally:
+        srv.close()
+    too_big = [r for r in reqs if r.error is not None]
+    assert all(r.dev["block"] > srv.arena.size for r in too_big)
+    assert st["requests"] == len(reqs) - len(too_big) > 250
+    assert fake.overlaps == 0
+    assert srv.arena.used == 0 and srv.arena.free == [(0, srv.arena.size)]
+    assert st["peak_device_bytes"] <= srv.arena.size
+    assert st["solo_rounds"] > 0 and st["rounds"] < st["requests"]
+    busy_streams = [si for _, _, si in fake.launches]
+    assert set(busy_streams) <= {0, 1, 2}
 
 
 gpu = pytest.mark.gpu
