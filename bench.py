@@ -6,13 +6,18 @@ growth, Wiener statistics, noise-variance reduction, Wiener apply) over one
 input of the chosen workload, through the C ABI.  Prints ONE JSON line.
 
 Workloads (seeded synthetic phantoms, see synth/):
-  paper1620  (default) 1620x1620 uint8, Gaussian sigma 20 + salt&pepper 0.20,
-             Smax 9, 5x5 Wiener, noise variance estimated.  The image is the
-             size of the paper's 2.5 MB medical image (Section V).
+  batched    (default) 256 uneven 12-bit slices (256^2..1024^2), per-slice
+             sigma, density, Smax and Wiener window; one persistent launch
+             replayed as a CUDA graph, against the per-slice launch loop
+             (also replayed from CUDA graphs) on the same slices.
+  paper1620  1620x1620 uint8, Gaussian sigma 20 + salt&pepper 0.20, Smax 9,
+             5x5 Wiener, noise variance estimated.  The image is the size of
+             the paper's 2.5 MB medical image (Section V).
   plain512   512x512 uint8, sigma 10, density 0.05, Smax 7, 3x3 Wiener.
   stress4096 4096x4096 12-bit, sigma 40, density 0.40, Smax 11, 5x5 Wiener.
-  batched    256 uneven 12-bit slices (256^2..1024^2), per-slice parameters,
-             one persistent launch replayed as a CUDA graph.
+  served     Poisson request stream (2000 req/s) over a pool of 256 images
+             512^2..4096^2 through the continuous-batching server: p50/p99
+             latency, throughput and a capacity sweep.
 With --parts P a single-image step runs the listing's partitioned median
 (hybrid_denoise_strips: P row strips median-filtered alone, then the Wiener
 filter of the whole image), as the paper runs it with P workers.
@@ -24,11 +29,13 @@ Timing: W untimed warm-up steps, then K steps between barrier +
 synchronize, timed with CUDA events on the launching stream.  Inputs rotate
 over enough device copies that every step reads data not resident in the
 129 MB L2.  `e2e` runs the same workload from pinned host buffers to pinned
-host buffers through the host pipeline (hd_host_pipeline: every step copies
-its image in and its result out inside the timed region, overlapping the
-neighbouring steps' kernels), and reports the one-blocking-call-a-step
-hybrid_denoise_host beside it.  `--impl reference` times the CPU oracle
-instead (bounded sample per step).
+host buffers through the library's host-buffer entry points (every step
+copies its inputs in and its results out inside the timed region).  The
+CPU legs (`cpu_baseline`, `accuracy`) run the oracle on the host cores: one
+thread on a bounded sample, and every core on the whole workload (or, for a
+single image, on row bands of it), where the oracle's outputs are also
+compared with the GPU's.  `--impl reference` times the oracle instead, on
+every host core (bounded sample per step).
 """
 from __future__ import annotations
 
@@ -57,6 +64,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 OPS_PER_PIXEL = 46
 ALU_LANES_PER_SM = 128          # 32-bit INT/FP32 lanes of one SM (4 partitions x 32)
 SM_MAX_GHZ = 2.07
+WORKLOADS = ["batched", "paper1620", "plain512", "stress4096", "served"]
 
 
 # --------------------------------------------------------------------------- helpers
@@ -98,6 +106,19 @@ def recorded_traffic(workload: str, source: str | None = None):
     if not ent or ent.get("source_hash") != want:
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def recorded_issue(workload: str):
+    """ncu instruction-issue figures of the persistent kernel for a workload
+    (if taken on the current kernel source): the measured side of the
+    integer-ALU roofline."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as fh:
+        ent = json.load(fh).get(workload)
+    if not ent or ent.get("source_hash") != kernel_source_hash() or "issue" not in ent:
+        return None
+    return ent["issue"]
 
 
 class ClockSampler:
@@ -186,35 +207,44 @@ def weak_value(px_per_rank: int, steps: int, max_ms: float, world: int) -> float
 
 
 # --------------------------------------------------------------------------- workloads
-def build_workload(name: str, rank: int):
-    """Host images + parameters.  Rank r draws its own replica (distinct seeds)."""
+SERVED_POOL = 256
+
+
+def workload_specs(name: str, rank: int):
+    """The seeded specs of a workload.  Rank r draws its own replica (distinct seeds)."""
     import synth
     if name in synth.CONFIGS:
         spec = synth.CONFIGS[name]
         if rank:
             spec = synth.SliceSpec(**{**spec.__dict__, "phantom_seed": spec.phantom_seed + 1000 * rank,
                                       "noise_seed": spec.noise_seed + 1000 * rank})
-        clean = spec.clean()
-        return [(spec, spec.noisy(clean))]
+        return [spec]
     if name == "batched":
-        specs = synth.batch_specs(256, master_seed=400 + rank)
-        return [(s, s.noisy()) for s in specs]
+        return synth.batch_specs(256, master_seed=400 + rank)
     if name == "served":
-        return served_pool(seed=501 + rank)
+        return synth.served_specs(SERVED_POOL, seed=501 + rank)
     raise SystemExit(f"unknown workload {name}")
+
+
+def build_workload(name: str, rank: int):
+    """[(spec, noisy host image)] of a workload (drawn on every host core)."""
+    import synth
+    specs = workload_specs(name, rank)
+    return list(zip(specs, synth.noisy_images(specs)))
 
 
 def describe(name: str, items, stretch: float | None = None, parts: int = 1) -> dict:
     px = sum(s.H * s.W for s, _ in items)
     if name == "served":
-        return {"workload": "served: pool of 16 seeded phantoms, side log-uniform [512, 4096], u8 / 12-bit "
-                            "50/50, s&p up to 0.3, Smax {5..11}, Wiener {3,5,7} (the reference arm denoises "
-                            "the pool's images one after another)", "images": len(items),
-                "megapixels": round(px / 1e6, 3)}
+        return {"workload": f"served: Poisson 2000 req/s over a pool of {len(items)} seeded phantoms, side "
+                            "log-uniform [512, 4096], u8 / 12-bit 50/50, s&p up to 0.3, Smax {5..11}, Wiener "
+                            "{3,5,7}, 8 GB device budget, continuous batching (3 rounds in flight)",
+                "images": len(items), "megapixels": round(px / 1e6, 3)}
     if name == "batched":
         return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
                             "density U[0.01,0.5], Smax {5,7,9,11}, Wiener {3,5,7}, one persistent launch "
-                            "(CUDA graph)", "images": len(items), "megapixels": round(px / 1e6, 3)}
+                            "(CUDA graph) vs the per-slice launch loop (CUDA graphs)",
+                "images": len(items), "megapixels": round(px / 1e6, 3)}
     s = items[0][0]
     d = {"workload": f"{name}: {s.H}x{s.W} {s.dtype} {s.bits}-bit, sigma {s.sigma:g}, s&p {s.density:g}, "
                      f"Smax {s.smax}, Wiener {s.wiener_w}x{s.wiener_w}, noise variance estimated",
@@ -254,11 +284,16 @@ def algorithmic_bytes(items) -> int:
     return sum(2 * s.H * s.W * (1 if s.dtype == "u8" else 2) for s, _ in items)
 
 
-# --------------------------------------------------------------------------- CPU oracle
+def digest(a: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
 def oracle_sample_rate(items, budget_s: float, stretch: float | None = None, parts: int = 1):
-    """Oracle Mpx/s on a bounded sample: whole images (or row bands) until ~budget_s.
-    With `stretch`, each band's result also goes through the oracle's contrast
-    stretch; with `parts` > 1 the band's median is partitioned."""
+    """Oracle Mpx/s on ONE host core, on a bounded sample: whole images (or row
+    bands) until ~budget_s.  With `stretch`, each band's result also goes
+    through the oracle's contrast stretch; with `parts` > 1 the band's median
+    is partitioned."""
     import oracle
 
     def run(g, spec):
@@ -296,31 +331,102 @@ def oracle_sample_rate(items, budget_s: float, stretch: float | None = None, par
     return done_px / t_total / 1e6, t_total, "; ".join(descr[:4]) + (" ..." if len(descr) > 4 else "")
 
 
+def accuracy_of(refs, gpu_out_sha, gpu_y_sha=None, gpu_nu2=None, specs=None) -> dict:
+    """The GPU results against the oracle's: bit-exact integer outputs and
+    binary32 values (by SHA-256), exact noise variances, and the binary32
+    value's distance from the binary64 definition."""
+    n = len(refs)
+    d = {"vs": "the oracle on the host cores: binary64 definition and its binary32 twin", "images": n,
+         "out_bit_exact_images": sum(r["out32_sha"] == h for r, h in zip(refs, gpu_out_sha))}
+    if gpu_y_sha is not None:
+        d["y32_bit_exact_images"] = sum(r["y32_sha"] == h for r, h in zip(refs, gpu_y_sha))
+    if gpu_nu2 is not None:
+        d["nu2_exact_images"] = sum(r["nu2"] == v for r, v in zip(refs, gpu_nu2))
+    d["max_abs_err_y32_vs_y64_lsb"] = max(r["max_err_y32_y64"] for r in refs)
+    if specs is not None:
+        d["bound_lsb"] = max(s.maxv for s in specs) * 2.0 ** -20
+    d["pixels_out_ne_round_y64"] = sum(r["round_diff"] for r in refs)
+    d["pixels"] = sum(r["pixels"] for r in refs)
+    return d
+
+
+def cpu_legs(items, budget_s: float, stretch=None, parts: int = 1, gpu=None):
+    """cpu_baseline (the oracle on every host core, plus one thread beside it)
+    and, when `gpu` gives the GPU's output digests, the accuracy record.
+
+    Every core: the whole workload (every image once, one image per worker),
+    or for a single image row bands of it; one thread: a bounded sample."""
+    from oracle import parallel
+    rate1, secs1, descr1 = oracle_sample_rate(items, budget_s, stretch, parts)
+    single = {"value": round(rate1, 4), "unit": "Mpixel/s", "cores": 1,
+              "sample": f"C oracle, one thread, {secs1:.1f} s on {descr1}"}
+    specs = [s for s, _ in items]
+    acc = None
+    with parallel.Runner() as runner:
+        if len(items) > 1:
+            refs = runner.run_specs(list(items))
+            rate, wall = parallel.rate_mpx(refs)
+            sample = f"the whole workload ({len(items)} images), one image per worker"
+        else:
+            spec, g = items[0]
+            bands = runner.run_bands(parallel.band_tasks(g, spec.smax, spec.wiener_w, spec.bits,
+                                                         rows=max(8, spec.H // (4 * runner.n))))
+            rate, wall = parallel.rate_mpx(bands)
+            sample = f"{spec.H}x{spec.W} in row bands with their halo rows, one band per task"
+            refs = runner.run_specs(list(items)) if gpu is not None and stretch is None and parts == 1 else None
+        cores = runner.n
+    if gpu is not None and refs is not None:
+        acc = accuracy_of(refs, *gpu, specs=specs)
+    cpu = {"value": round(rate, 4), "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+           "sample": f"C oracle (unchanged) on {cores} host cores, {wall:.1f} s wall: {sample}"
+                     + ("; the hybrid only (no stretch, no strips)" if (stretch is not None or parts > 1) else ""),
+           "single_thread": single}
+    return cpu, acc
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands, on every host core of the box: each step a
+    bounded sample of the workload (whole images one per worker, or row bands
+    of a single image)."""
     if rank != 0:
         return 0
-    import oracle
-    oracle.build()
-    items = build_workload(args.workload, 0)
-    per_step = max(0.2, min(5.0, args.ref_budget / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_sample_rate(items, per_step, args.stretch, args.parts)
-    rates, tsum, descr = [], 0.0, ""
-    for _ in range(args.steps):
-        r, t, descr = oracle_sample_rate(items, per_step, args.stretch, args.parts)
-        rates.append(r)
-        tsum += t
+    from oracle import parallel
+    import synth
+    specs = workload_specs(args.workload, 0)
+    per_step = max(0.3, min(10.0, args.ref_budget / max(1, args.steps + args.warmup)))
+    rates = []
+    with parallel.Runner() as runner:
+        # the sample: row bands (with their halo rows) of the first images of
+        # the workload, rotating; a step takes as many bands as fit its budget
+        # (calibrated by the steps before it)
+        imgs = synth.noisy_images(specs[:max(1, min(len(specs), 2 * runner.n))])
+        tasks = []
+        for spec, g in zip(specs, imgs):
+            tasks += parallel.band_tasks(g, spec.smax, spec.wiener_w, spec.bits, rows=32)
+        take, pos = runner.n, 0
+        for k in range(args.warmup + args.steps):
+            sub = [tasks[(pos + i) % len(tasks)] for i in range(take)]
+            pos += take
+            res = runner.run_bands(sub)
+            rate, wall = parallel.rate_mpx(res)
+            if k >= args.warmup:
+                rates.append(rate)
+            take = int(min(4 * len(tasks), max(runner.n, take * per_step / max(wall, 1e-3))))
+        descr = (f"about {take} row bands of 32 rows (with halo rows) a step, from the first {len(imgs)} "
+                 f"images of the workload, one band per task")
+        cores = runner.n
     value = statistics.median(rates)
-    px_step = describe(args.workload, items)["megapixels"]
+    px_step = describe(args.workload, [(s, None) for s in specs])["megapixels"]
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * px_step / value, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic",
-        "dtype": "u8+u16" if args.workload == "served" else ("u8" if items[0][0].dtype == "u8" else "u16"),
-        "config": describe(args.workload, items, args.stretch, args.parts),
-        "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step ~{per_step:.1f} s of the C oracle (single thread) on {descr}"},
+        "dtype": "u8+u16" if args.workload == "served" else ("u8" if specs[0].dtype == "u8" else "u16"),
+        "config": describe(args.workload, [(s, None) for s in specs], args.stretch, args.parts),
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step ~{per_step:.1f} s of the C oracle on {cores} host cores: {descr}"
+                                   + ("; the hybrid only" if (args.stretch is not None or args.parts > 1) else "")},
         "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -328,95 +434,101 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------- served
-def served_pool(n: int = 16, seed: int = 501):
-    """Pool of requests: side log-uniform in [512, 4096], u8 or 12-bit 50/50,
-    sigma U[5,25] (u8) / U[10,60] (12-bit), salt & pepper density U[0, 0.3]."""
-    import synth
-    rng = np.random.default_rng(seed)
-    pool = []
-    for i in range(n):
-        side = int(np.exp(rng.uniform(np.log(512), np.log(4096))))
-        H = side
-        W = int(side * rng.uniform(0.8, 1.25)) // 2 * 2
-        if i % 2 == 0:
-            spec = synth.SliceSpec(H, W, "u8", 8, float(rng.uniform(5, 25)), float(rng.uniform(0, 0.3)),
-                                   int(rng.choice([5, 7, 9, 11])), int(rng.choice([3, 5, 7])),
-                                   seed * 1000 + i, seed * 1000 + 500 + i, kind="ellipse")
-        else:
-            spec = synth.SliceSpec(H, W, "u16", 12, float(rng.uniform(10, 60)), float(rng.uniform(0, 0.3)),
-                                   int(rng.choice([5, 7, 9, 11])), int(rng.choice([3, 5, 7])),
-                                   seed * 1000 + i, seed * 1000 + 500 + i, kind="ct")
-        pool.append((spec, spec.noisy()))
-    return pool
-
-
 def run_served(args, rank, world, dev, hd, torch):
-    """Poisson request stream (2000 req/s) through the continuous-batching server."""
+    """Poisson request stream (2000 req/s) through the continuous-batching
+    server: 2 s of warm-up arrivals, then `--served-seconds` of arrivals;
+    then a capacity sweep of short runs at higher rates."""
     from paper_2005_05371_gb300.serve import Server, poisson_arrivals, replay
-    pool = served_pool()
-    hosts = [torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory() for _, g in pool]
+    items = build_workload("served", rank)
+    specs = [s for s, _ in items]
+    hosts = [torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory() for _, g in items]
     outs = [torch.empty_like(h).pin_memory() for h in hosts]
 
     def params_of(i):
-        s = pool[i % len(pool)][0]
+        s = specs[i % len(specs)]
         return hd.Params(s.smax, s.wiener_w, -1.0, hd.HD_BORDER_SYMMETRIC, hd.HD_UNRESOLVED_ZMED, s.bits)
 
     from paper_2005_05371_gb300 import autotune
     tuning = autotune.choose_batch()
     hd.hd_set_tuning(*tuning)
+    rate = 2000.0
+    bound_ms = 50.0
+
+    def run(srv, r_hz, seconds, seed):
+        n = max(1, int(r_hz * seconds))
+        reqs = replay(srv, hosts, poisson_arrivals(r_hz, n, seed), params_of, outs=outs)
+        for r in reqs:
+            r.done.wait(600)
+        lat = np.array([r.latency_ms for r in reqs if r.error is None])
+        px = sum(r.pixels for r in reqs if r.error is None)
+        span = max(r.t_done for r in reqs) - min(r.t_arrive for r in reqs)
+        return reqs, {"offered_req_s": r_hz, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)), 3), "mpixel_s": round(px / span / 1e6, 1),
+                      "requests": len(reqs)}
+
     srv = Server(budget_bytes=8 << 30, max_inflight=3, device=dev)
     try:
-        warm = replay(srv, hosts, poisson_arrivals(2000.0, max(args.warmup, 3) * 10, 499), params_of)
-        for r in warm:
-            r.done.wait(120)
+        run(srv, rate, 2.0, 499)                            # warm-up: 2 s of arrivals
         srv.finished.clear()
-        n_req = args.steps * 40
-        arrivals = poisson_arrivals(2000.0, n_req, 500 + rank)
+        srv.rounds = srv.solo_rounds = 0
         with ClockSampler(dev.index or 0) as clk:
-            reqs = []
-            t0 = time.perf_counter()
-            for i, t in enumerate(arrivals):
-                # sleep to the arrival time: a busy wait would hold the
-                # interpreter lock that the scheduler thread needs
-                wait = t - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
-                j = i % len(hosts)
-                reqs.append(srv.submit(hosts[j], params_of(j), outs[j]))
-            for r in reqs:
-                r.done.wait(300)
+            reqs, main = run(srv, rate, args.served_seconds, 500 + rank)
         st = srv.stats()
         clocks = clk.summary()
         clocks["window"] = "request stream"
+        # capacity: the highest offered rate whose p99 stays under the bound and
+        # whose served rate keeps up with the offered one
+        sweep, capacity = [], None
+        for k, r_hz in enumerate((2000.0, 4000.0, 6000.0, 8000.0, 12000.0, 16000.0)):
+            _, res = run(srv, r_hz, 2.0, 600 + k)
+            offered_mpx = r_hz * sum(s.H * s.W for s in specs) / len(specs) / 1e6
+            res["keeps_up"] = res["mpixel_s"] >= 0.9 * offered_mpx
+            sweep.append(res)
+            if res["p99_ms"] <= bound_ms and res["keeps_up"]:
+                capacity = res
+            else:
+                break
     finally:
         srv.close()
     status = hd.hd_get_device_error()
     if status != hd.HD_OK:
         raise SystemExit(f"device error: {hd.hd_status_str(status)}")
+    n_req = len(reqs)
     px = sum(r.pixels for r in reqs)
-    bytes_in = sum(int(r.host.numel() * r.host.element_size()) for r in reqs)
+    bytes_in = sum(r.nbytes for r in reqs)
     span_ms = 1e3 * (max(r.t_done for r in reqs) - min(r.t_arrive for r in reqs))
     span_ms = max_over_ranks(span_ms, dev)
     value = weak_value(px, 1, span_ms, world)
     peak, peak_kind = peaks()
     achieved = 2 * bytes_in / (span_ms / 1e3) / 1e9
+    cpu = acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # every pool image was served (the stream cycles through the pool);
+        # the oracle checks the first 32 results and gives the CPU baseline
+        sub = items[:32]
+        got = [o.numpy().view(np.uint16) if s.dtype == "u16" else o.numpy() for o, (s, _) in zip(outs, sub)]
+        cpu, acc = cpu_legs(sub, args.cpu_budget, gpu=([digest(a) for a in got],))
+        cpu["sample"] += " (the first 32 pool images)"
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": n_req,
-            "warmup": len(warm), "ms_per_step": round(span_ms / n_req, 5), "higher_is_better": True,
+            "warmup": int(rate * 2.0), "ms_per_step": round(span_ms / n_req, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
-            "config": {"workload": "served: Poisson 2000 req/s, pool of 16 seeded phantoms, side log-uniform "
-                                   "[512, 4096], u8 / 12-bit 50/50, s&p up to 0.3, Smax {5..11}, Wiener {3,5,7}, "
-                                   "8 GB device budget, continuous batching (3 rounds in flight)",
-                       "requests": n_req, "megapixels": round(px / 1e6, 1), "parallelism": f"replicas x{world}",
+            "config": {**describe("served", items), "requests": n_req, "seconds_of_arrivals": args.served_seconds,
+                       "warmup_seconds": 2.0, "megapixels": round(px / 1e6, 1), "parallelism": f"replicas x{world}",
                        "tuning": {"region_h": tuning[0], "ctas_per_sm": tuning[1]},
-                       "l2": "every request moves its own input/output through HBM (pool 16 images, ~120 MB)"},
+                       "l2": f"every request moves its own input/output through HBM (pool {len(items)} images, "
+                             f"{sum(h.numel() * h.element_size() for h in hosts) / 1e9:.1f} GB)"},
             "latency": {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                        "rounds": st["rounds"], "peak_device_bytes": st["peak_device_bytes"]},
+                        "rounds": st["rounds"], "solo_rounds": st["solo_rounds"],
+                        "peak_device_bytes": st["peak_device_bytes"]},
+            "capacity": {"p99_bound_ms": bound_ms, "highest_rate_within_bound": capacity, "sweep": sweep,
+                         "run_seconds": 2.0},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "kernel": "hd_persistent_kernel",
-                         "peak_kind": peak_kind},
-            "cpu_baseline": None,
+                         "peak_kind": peak_kind,
+                         "note": "served rate equals the offered load at 2000 req/s: see capacity"},
+            "cpu_baseline": cpu, "accuracy": acc,
             "e2e": {"value": round(value, 2), "unit": "Mpixel/s", "h2d_bytes_per_step": bytes_in // n_req,
                     "d2h_bytes_per_step": bytes_in // n_req,
                     "api": "Server.submit (pinned host in/out, copies and launches inside)"},
@@ -433,10 +545,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="paper1620",
-                    choices=["paper1620", "plain512", "stress4096", "batched", "served"])
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--workload", default="batched", choices=WORKLOADS)
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of single-thread oracle work")
     ap.add_argument("--ref-budget", type=float, default=90.0, help="total seconds of the reference arm")
+    ap.add_argument("--served-seconds", type=float, default=10.0, help="seconds of arrivals of the served run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parts", type=int, default=1,
@@ -462,7 +574,6 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    sys.path.insert(0, ROOT)
     import __graft_entry__
     __graft_entry__._buildlib().build()
     import paper_2005_05371_gb300 as hd
@@ -471,13 +582,11 @@ def main():
         return run_served(args, rank, world, dev, hd, torch)
 
     items = build_workload(args.workload, rank)
+    batched = args.workload == "batched"
     cfg = describe(args.workload, items, args.stretch, args.parts)
     # work-item shape from the autotuner's table (paper_2005_05371_gb300/tuning.json)
     from paper_2005_05371_gb300 import autotune
-    if args.workload == "batched":
-        tuning = autotune.choose_batch()
-    else:
-        tuning = autotune.choose(items[0][0].H, items[0][0].W)
+    tuning = autotune.choose_batch() if batched else autotune.choose(items[0][0].H, items[0][0].W)
     hd.hd_set_tuning(*tuning)
     cfg["tuning"] = {"region_h": tuning[0], "ctas_per_sm": tuning[1]}
     stream = torch.cuda.current_stream(dev)
@@ -489,11 +598,14 @@ def main():
     def params_of(spec):
         return hd.Params(spec.smax, spec.wiener_w, -1.0, hd.HD_BORDER_SYMMETRIC, hd.HD_UNRESOLVED_ZMED, spec.bits)
 
+    def code_of(spec):
+        return hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
+
     step_bytes = algorithmic_bytes(items)
-    copies = max(1, math.ceil(3 * L2_BYTES / step_bytes)) if args.workload != "batched" else 2
+    copies = 2 if batched else max(1, math.ceil(3 * L2_BYTES / step_bytes))
     px_per_step = sum(s.H * s.W for s, _ in items)
 
-    if args.workload == "batched":
+    if batched:
         # `copies` independent batch plans over distinct device buffers
         plans, bufs = [], []
         for c in range(copies):
@@ -509,22 +621,27 @@ def main():
             plans[i % copies].launch(s)
 
         launches_per_step = 1
-        # plain: per-slice launch loop (one hybrid_denoise call per slice) on the same data
-        spec0 = None
-        ws_plain = [hd._workspace(hd.hybrid_workspace_size(s.H, s.W, hd.HD_U16, params_of(s)), dev)
+        # plain: the per-slice launch loop (one hybrid_denoise call per slice, each
+        # with its size class's tuning and a full workspace) on the same data
+        ws_plain = [hd._workspace(hd.hybrid_workspace_size(s.H, s.W, code_of(s), params_of(s)), dev)
                     for s, _ in items]
+        slice_tuning = [autotune.choose(s.H, s.W) for s, _ in items]
 
         def plain_step(i, s):
             its = bufs[i % copies]
-            for (src, dst, p), ws in zip(its, ws_plain):
-                hd.hybrid_denoise(src, dst, p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
-                                  workspace=ws, stream=s)
+            try:
+                for (src, dst, p), ws, tn in zip(its, ws_plain, slice_tuning):
+                    hd.hd_set_tuning(*tn)
+                    hd.hybrid_denoise(src, dst, p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                                      workspace=ws, stream=s)
+            finally:
+                hd.hd_set_tuning(*tuning)
     else:
         spec, g = items[0]
         p = params_of(spec)
         srcs = [to_dev(g) for _ in range(copies)]
         dsts = [torch.empty_like(srcs[0]) for _ in range(copies)]
-        code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
+        code = code_of(spec)
         if args.parts > 1:
             ws = hd._workspace(hd.hybrid_strips_workspace_size(spec.H, spec.W, code, p, args.parts), dev)
 
@@ -561,8 +678,6 @@ def main():
 
             launches_per_step += 1
 
-    use_graph = args.workload != "batched"
-
     def capture(fn, first, count):
         """One CUDA graph holding `count` consecutive steps."""
         g = torch.cuda.CUDAGraph()
@@ -575,16 +690,17 @@ def main():
         stream.wait_stream(cs)
         return g
 
-    def timed(fn, K, W, graph):
+    def timed(fn, K, W, graph, per_graph=400):
         """K steps after W warm-up steps; CUDA events on the launching stream.
-        With graph=True the K steps replay from CUDA graphs (launch overhead of
-        the host path is not timed; every step is still one kernel launch)."""
+        With graph=True the K steps replay from CUDA graphs of up to
+        `per_graph` steps each (the host's launch cost is not timed; every
+        kernel still launches)."""
         for i in range(W):
             fn(i, stream)
         torch.cuda.synchronize(dev)
         plan = []
         if graph:
-            G = min(K, 400)
+            G = min(K, per_graph)
             g_main = capture(fn, W, G)
             plan = [g_main] * (K // G)
             if K % G:
@@ -622,8 +738,9 @@ def main():
                     fn(0, stream)
                 torch.cuda.synchronize(dev)
 
+    # a batch plan is itself a CUDA graph: its steps launch directly
     with ClockSampler(local) as clk:
-        total_ms, graphs, wall = timed(step, args.steps, args.warmup, use_graph)
+        total_ms, graphs, wall = timed(step, args.steps, args.warmup, not batched)
         soaked = max(0.0, 1.5 - wall)
         if soaked > 0:
             soak(step, graphs, soaked)
@@ -638,7 +755,7 @@ def main():
     value = weak_value(px_per_step, args.steps, total_ms, world)
 
     # dominant kernel: one persistent launch per step; events over
-    # back-to-back launches (graph replay) give the average launch duration
+    # back-to-back launches give the average launch duration
     peak, peak_kind = peaks()
     extra = {}
     hybrid_ms = ms_per_step
@@ -662,13 +779,13 @@ def main():
     # the integer/FP32 side of the roofline: algorithmic operations per pixel
     # of the 3x3 median stage and the Wiener stage (window growth not
     # counted, so this is a lower bound of the work) against the SMs' 32-bit
-    # lanes at the maximum SM clock
+    # lanes at the maximum SM clock; the measured issue rate from ncu beside it
     props = torch.cuda.get_device_properties(dev)
     alu_peak = props.multi_processor_count * ALU_LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
     alu_achieved = px_per_step * OPS_PER_PIXEL / (hybrid_ms / 1e3) / 1e12
+    traffic = recorded_traffic(args.workload) if args.parts == 1 else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": recorded_traffic(args.workload) if args.parts == 1 else None,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": "hd_persistent_kernel", "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": step_bytes}
@@ -676,18 +793,27 @@ def main():
                     "unit": "Tops/s", "frac": round(alu_achieved / alu_peak, 4),
                     "ops_per_pixel": OPS_PER_PIXEL, "kernel": "hd_persistent_kernel",
                     "peak_kind": f"derived: {props.multi_processor_count} SMs x {ALU_LANES_PER_SM} lanes x "
-                                 f"{SM_MAX_GHZ} GHz"}
+                                 f"{SM_MAX_GHZ} GHz",
+                    "ncu_issue": recorded_issue(args.workload) if args.parts == 1 else None}
 
-    if plain_step is not None:
-        plain_ms, _, _ = timed(plain_step, max(3, args.steps // 5), args.warmup, False)
-        extra["plain_loop"] = {"value": round(px_per_step * max(3, args.steps // 5) / (plain_ms / 1e3) / 1e6, 1),
-                               "unit": "Mpixel/s", "launches_per_step": len(items)}
+    if batched:
+        # the plain per-slice loop, replayed from CUDA graphs of 4 steps (1024 launches each)
+        Kp = max(4, args.steps // 5 // 4 * 4)
+        plain_ms, _, _ = timed(plain_step, Kp, 2, True, per_graph=4)
+        plain_ms = max_over_ranks(plain_ms, dev)
+        plain_value = weak_value(px_per_step, Kp, plain_ms, world)
+        extra["plain_loop"] = {"value": round(plain_value, 1), "unit": "Mpixel/s",
+                               "ms_per_step": round(plain_ms / Kp, 4), "launches_per_step": len(items),
+                               "how": "one hybrid_denoise per slice (its size class's tuning, full workspace), "
+                                      "replayed from CUDA graphs", "batched_over_plain": round(value / plain_value, 3)}
+        status = hd.hd_get_device_error(stream)
+        if status != hd.HD_OK:
+            raise SystemExit(f"device error in the plain loop: {hd.hd_status_str(status)}")
 
-    # end to end through the host-buffer entry point
+    # end to end through the library's host-buffer entry points
     e2e = None
     if not args.no_e2e and (args.stretch is not None or args.parts > 1):
-        # end to end through the public calls: pinned host -> device, hybrid,
-        # stretch, device -> pinned host, wait
+        # pinned host -> device, hybrid (strips), stretch, device -> pinned host, wait
         spec, g = items[0]
         hsrc = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory()
         hdst = torch.empty_like(hsrc).pin_memory()
@@ -709,13 +835,13 @@ def main():
                "h2d_bytes_per_step": g.nbytes, "d2h_bytes_per_step": g.nbytes,
                "api": "copy_ + " + ("hybrid_denoise_strips" if args.parts > 1 else "hybrid_denoise") +
                       (" + contrast_stretch" if args.stretch is not None else "") + " (pinned host buffers)"}
-    elif not args.no_e2e and args.workload != "batched":
-        # end to end through the host pipeline: every step copies its noisy
-        # image in from pinned host memory and its result back out, and the
-        # copies of one step overlap the kernels of its neighbours
+    elif not args.no_e2e and not batched:
+        # the host pipeline: every step copies its noisy image in from pinned
+        # host memory and its result back out; the copies of one step overlap
+        # the kernels of its neighbours
         spec, g = items[0]
         p = params_of(spec)
-        code = hd.HD_U8 if spec.dtype == "u8" else hd.HD_U16
+        code = code_of(spec)
         hsrc = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).pin_memory()
         hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(2)]
         pipe = hd.HostPipeline(spec.H, spec.W, code, p, depth=2, device=dev)
@@ -741,72 +867,72 @@ def main():
         e2e["synchronous_call"] = {"value": round(world * px_per_step * K3 / (time.perf_counter() - t0) / 1e6, 2),
                                    "api": "hybrid_denoise_host, one blocking call a step"}
     elif not args.no_e2e:
-        # batched end to end: all slices in one pinned host buffer and one
-        # device buffer, so a step is one copy in, one plan launch and one copy
-        # out; two buffer sets on two streams let one step's copies overlap the
-        # other's kernel
+        # the batch pipeline: every step copies all slices in from one pinned
+        # host buffer (back to back: one copy) and the results back out;
+        # depth 2, so one step's copies overlap its neighbours' kernels
         sizes = [g.size for _, g in items]
-        offs = np.concatenate([[0], np.cumsum(sizes)])
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         h_in = torch.empty(int(offs[-1]), dtype=torch.int16).pin_memory()
         for (_, g), o in zip(items, offs[:-1]):
             h_in[int(o):int(o) + g.size].copy_(torch.from_numpy(g.view(np.int16).reshape(-1)))
         h_out = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
-        sets = []
-        for k in range(2):
-            d_in, d_out = torch.empty(int(offs[-1]), dtype=torch.int16, device=dev), torch.empty(
-                int(offs[-1]), dtype=torch.int16, device=dev)
-            its = [(d_in[int(o):int(o) + s.H * s.W].view(s.H, s.W), d_out[int(o):int(o) + s.H * s.W].view(s.H, s.W),
-                    params_of(s)) for (s, _), o in zip(items, offs[:-1])]
-            sets.append((d_in, d_out, hd.BatchPlan(its), torch.cuda.Stream(dev)))
-
-        def e2e_step(i):
-            d_in, d_out, plan, st = sets[i % 2]
-            with torch.cuda.stream(st):
-                d_in.copy_(h_in, non_blocking=True)
-                plan.launch(st)
-                h_out[i % 2].copy_(d_out, non_blocking=True)
+        views = lambda buf: [buf[int(o):int(o) + s.H * s.W].view(s.H, s.W) for (s, _), o in zip(items, offs[:-1])]
+        in_v, out_v = views(h_in), [views(h) for h in h_out]
+        pipe = hd.BatchPipeline([(s.H, s.W, code_of(s), params_of(s)) for s, _ in items], depth=2, device=dev)
         for i in range(args.warmup):
-            e2e_step(i)
-        torch.cuda.synchronize(dev)
+            pipe.submit(in_v, out_v[i % 2])
+        pipe.wait()
         t0 = time.perf_counter()
-        K2 = max(3, args.steps // 5)
-        for i in range(K2):
-            e2e_step(i)
-        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            pipe.submit(in_v, out_v[i % 2])
+        pipe.wait()
         dt = time.perf_counter() - t0
-        for _, _, plan, _ in sets:
-            plan.close()
+        pipe.close()
         nb = sum(g.nbytes for _, g in items)
-        e2e = {"value": round(world * px_per_step * K2 / dt / 1e6, 2), "unit": "Mpixel/s",
+        e2e = {"value": round(world * px_per_step * args.steps / dt / 1e6, 2), "unit": "Mpixel/s",
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-               "api": "one copy in + hd_batch_plan_launch + one copy out a step (pinned host buffers, "
-                      "two buffer sets on two streams)"}
+               "api": "hd_batch_pipeline (pinned host buffers, all slices back to back: one copy each way a "
+                      "step; depth 2)"}
+        status = hd.hd_get_device_error()
+        if status != hd.HD_OK:
+            raise SystemExit(f"device error in the batch pipeline: {hd.hd_status_str(status)}")
 
-    # output quality against the clean phantoms, from one more step outside the
-    # timed region (the hybrid output, before any contrast stretch)
+    # one more step outside the timed region, with the binary32 values and noise
+    # variances kept, for the oracle comparison and the quality figures
     def host_image(t, spec):
         a = t.cpu().numpy()
         return a.view(np.uint16) if spec.dtype != "u8" else a
-    if args.workload == "batched":
-        plans[0].launch(stream)
+    gpu_rec = None
+    if batched:
+        nv = torch.full((len(items),), -7.0, dtype=torch.float64, device=dev)
+        ys = [torch.empty((s.H, s.W), dtype=torch.float32, device=dev) for s, _ in items]
+        imgs = [hd.make_image(src, dst, pp, nv[i:i + 1], ys[i]) for i, (src, dst, pp) in enumerate(bufs[0])]
+        hd.hybrid_denoise_batched(imgs, stream=stream)
         torch.cuda.synchronize(dev)
         outs = [host_image(dst, spec) for (_, dst, _), (spec, _) in zip(bufs[0], items)]
+        gpu_rec = ([digest(o) for o in outs], [digest(y.cpu().numpy()) for y in ys], nv.cpu().tolist())
+        del ys
         extra["quality"] = quality(outs, [spec.clean() for spec, _ in items], [g for _, g in items], 12)
     else:
-        hybrid_step(0, stream)
-        torch.cuda.synchronize(dev)
         spec0, g0 = items[0]
-        extra["quality"] = quality([host_image(dsts[0], spec0)], [spec0.clean()], [g0], spec0.bits)
+        nv = torch.full((1,), -7.0, dtype=torch.float64, device=dev)
+        y = torch.empty((spec0.H, spec0.W), dtype=torch.float32, device=dev)
+        hd.hybrid_denoise(srcs[0], dsts[0], p.smax, p.wiener_w, p.noise_var, p.border, p.unresolved, p.bits,
+                          noise_var_out=nv, y_out=y, stream=stream)
+        torch.cuda.synchronize(dev)
+        out0 = host_image(dsts[0], spec0)
+        gpu_rec = ([digest(out0)], [digest(y.cpu().numpy())], nv.cpu().tolist())
+        extra["quality"] = quality([out0], [spec0.clean()], [g0], spec0.bits)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, descr = oracle_sample_rate(items, args.cpu_budget, args.stretch, args.parts)
-        cpu = {"value": round(rate, 4), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-               "sample": f"C oracle, single thread, {secs:.1f} s on {descr}"}
+        cpu, acc = cpu_legs(items, args.cpu_budget, args.stretch, args.parts, gpu=gpu_rec)
+        if acc is not None:
+            extra["accuracy"] = acc
         # the paper's parallel metrics (Section 3.3): T_s = the serial oracle's
         # time for one step's pixels, T_p = this GPU's step, P = its SMs
-        t_s = px_per_step / (rate * 1e6) * 1e3
-        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        t_s = px_per_step / (cpu["single_thread"]["value"] * 1e6) * 1e3
+        n_sm = props.multi_processor_count
         s_p = t_s / ms_per_step
         extra["paper_metrics"] = {"T_s_ms": round(t_s, 3), "T_p_ms": round(ms_per_step, 5), "P": n_sm,
                                   "S_P": round(s_p, 1), "EFF": round(s_p / n_sm, 2),

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "ellipse_phantom", "ct_phantom", "add_noise", "SliceSpec", "batch_specs",
-    "config_image", "CONFIGS",
+    "config_image", "CONFIGS", "served_specs", "noisy_images",
 ]
 
 
@@ -202,3 +202,47 @@ def batch_specs(n: int = 256, master_seed: int = 400) -> list[SliceSpec]:
                              int(rng.choice([3, 5, 7])), 1000 * master_seed + i, 1000 * master_seed + 100000 + i,
                              kind="ct"))
     return out
+
+
+def served_specs(n: int = 256, seed: int = 501) -> list[SliceSpec]:
+    """Request pool of the served workload: side log-uniform in [512, 4096]
+    (width 0.8-1.25 x the height, even), uint8 and 12-bit alternating, sigma
+    U[5,25] (uint8) / U[10,60] (12-bit), salt & pepper density U[0, 0.3], Smax
+    in {5,7,9,11}, Wiener window in {3,5,7}.  Image i uses phantom seed
+    1000*seed+i and noise seed 1000*seed+500+i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(np.exp(rng.uniform(np.log(512), np.log(4096))))
+        H = side
+        W = int(side * rng.uniform(0.8, 1.25)) // 2 * 2
+        if i % 2 == 0:
+            out.append(SliceSpec(H, W, "u8", 8, float(rng.uniform(5, 25)), float(rng.uniform(0, 0.3)),
+                                 int(rng.choice([5, 7, 9, 11])), int(rng.choice([3, 5, 7])),
+                                 seed * 1000 + i, seed * 1000 + 500 + i, kind="ellipse"))
+        else:
+            out.append(SliceSpec(H, W, "u16", 12, float(rng.uniform(10, 60)), float(rng.uniform(0, 0.3)),
+                                 int(rng.choice([5, 7, 9, 11])), int(rng.choice([3, 5, 7])),
+                                 seed * 1000 + i, seed * 1000 + 500 + i, kind="ct"))
+    return out
+
+
+def _noisy_of(spec: SliceSpec) -> np.ndarray:
+    return spec.noisy()
+
+
+def noisy_images(specs, processes: int | None = None) -> list[np.ndarray]:
+    """The noisy images of many specs, drawn on ``processes`` spawned workers
+    (default: every host core); the same arrays as ``[s.noisy() for s in specs]``."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    n = max(1, min(processes or cores, len(specs)))
+    if n == 1:
+        return [s.noisy() for s in specs]
+    with ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_noisy_of, specs, chunksize=1))
