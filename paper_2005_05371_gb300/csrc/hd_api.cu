@@ -287,6 +287,23 @@ struct BatchTables {
     size_t table_bytes = 0;   // bytes from ctl_off to the end of the segment table
 };
 
+// Wiener tiles of an image are queued this many grids of tickets after its
+// last median tile (see build_batch).
+constexpr int kBatchLagGrids = 3;
+
+// Grid of a batched launch with the current tuning (as finish_params sizes it).
+long long batch_grid(const BatchTables &bt)
+{
+    const hd_tuning t = current_tuning();
+    const size_t smem = smem_bytes(t.region_h, bt.ra_max, bt.wide);
+    const int sms = device_sms();
+    int per_sm = smem <= 227 * 1024 ? max_ctas_per_sm(smem) : 0;
+    if (t.ctas_per_sm > 0 && per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
+    // no device answer (sizes only): a grid of one GB300 at 3 CTAs per SM
+    if (sms <= 0 || per_sm <= 0) return 152LL * 3;
+    return (long long)sms * per_sm;
+}
+
 hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, BatchTables &bt,
                       BatchLayout &L)
 {
@@ -311,8 +328,13 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
         bt.wide |= image_wide(bt.descs[i]) ? 1 : 0;
     }
 
-    // ticket order: P1(0), P1(1), P2(0), P1(2), P2(1), ..., P2(n-1).  An image's
-    // Wiener tiles follow its median tiles with one image of lag, so they seldom wait.
+    // ticket order: every image's median tiles (P1) in image order; an image's
+    // Wiener tiles (P2) follow once `lag` more median tiles have been queued
+    // after its last one, or at the end.  A P2 tile waits for all of its
+    // image's P1 tiles, and those were handed out `lag` tickets earlier:
+    // with lag a few times the grid, they are done by the time it starts,
+    // so the wait is rarely more than one poll.
+    const long long lag = (long long)kBatchLagGrids * batch_grid(bt);
     long long first = 0;
     auto push = [&](int img, int phase) {
         const ImgDesc &d = bt.descs[img];
@@ -320,11 +342,16 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
         bt.segs.push_back(Seg{img, phase, (int)first, items});
         first += items;
     };
+    std::vector<long long> p1_end(n, 0);
+    std::vector<int> pending;           // images whose P2 is not placed yet, in order
+    size_t head = 0;
     for (int i = 0; i < n; ++i) {
         push(i, 1);
-        if (i >= 1 && mode_two_phase(bt.descs[i - 1].mode)) push(i - 1, 2);
+        p1_end[i] = first;
+        if (mode_two_phase(bt.descs[i].mode)) pending.push_back(i);
+        while (head < pending.size() && first - p1_end[pending[head]] >= lag) push(pending[head++], 2);
     }
-    if (mode_two_phase(bt.descs[n - 1].mode)) push(n - 1, 2);
+    while (head < pending.size()) push(pending[head++], 2);
     if (first > 0x7fffffffLL) return HD_ERR_OVERFLOW;
     bt.total_items = (int)first;
     bt.table_bytes = L.seg_off + sizeof(Seg) * bt.segs.size() - L.ctl_off;

@@ -270,12 +270,14 @@ class Server:
             self.admitted.append(r)
             self.peak_used = max(self.peak_used, self.arena.used)
 
-    def _launch_round(self):
+    def _launch_round(self) -> bool:
         """Launch admitted requests (up to max_batch) as one batched kernel.
         A round of several needs a workspace gap in the arena (the round is
-        halved until one fits); otherwise the first request runs alone in its
-        own block."""
+        halved until one fits).  A lone request, or the first request when no
+        gap fits and no round is running to free one, runs alone in its own
+        block.  Returns False when the round has to wait for space."""
         take = min(len(self.admitted), self.max_batch)
+        lone = take == 1
         a_ws = None
         while take >= 2:
             reqs = [self.admitted[i] for i in range(take)]
@@ -284,6 +286,8 @@ class Server:
                 break
             take //= 2
         if a_ws is None:
+            if not lone and self.inflight:
+                return False          # running rounds will free space
             take = 1
             reqs = [self.admitted[0]]
             ws_off, ws_len = reqs[0].dev["ws"], reqs[0].dev["ws_len"]
@@ -298,6 +302,7 @@ class Server:
         self.inflight.append((ev, reqs, a_ws, si))
         self.rounds += 1
         self.peak_used = max(self.peak_used, self.arena.used)
+        return True
 
     def _retire(self):
         still = []
@@ -328,7 +333,8 @@ class Server:
                 self._retire()
                 self._admit()
                 while self.admitted and len(self.inflight) < self.max_inflight:
-                    self._launch_round()
+                    if not self._launch_round():
+                        break
                 idle = not self.admitted and not self.waiting
             if idle and not self.inflight:
                 with self.lock:
