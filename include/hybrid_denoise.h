@@ -336,16 +336,35 @@ hd_status hd_batch_pipeline_wait(hd_batch_pipeline *pipeline);
 hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pipeline);
 
 /* ---------------------------------------------------------------- tuning
- * Work-item shape of the persistent kernel.  Each item covers a region of
- * 64 columns x region_h rows of the median output; its output tile is that
- * region less the Wiener halo, (64 - 2*(w/2)) x (region_h - 2*(w/2)).
- * region_h: multiple of 8 in [16, 128] (default 32).  ctas_per_sm: grid size
- * per SM, 1..8, 0 = as many as fit.  reserved must be 0.  Applies to later
- * launches in this process; results do not depend on it. */
+ * Work-item shape and scheduling of the persistent kernel; the autotuner
+ * (paper_2005_05371_gb300/autotune.py) picks them per workload class.  Each
+ * item covers a region of 64 columns x region_h rows of the median output;
+ * its output tile is that region less the Wiener halo,
+ * (64 - 2*(w/2)) x (region_h - 2*(w/2)).  The 64 columns are fixed: each of
+ * a warp's 32 lanes owns one pixel pair of a region row.
+ *   region_h:     multiple of 8 in [16, 128] (default 32).
+ *   ctas_per_sm:  grid size per SM, 1..8, 0 = as many as fit.
+ *   plane:        0 = a single image uses the statistics plane whenever its
+ *                 workspace has room for it; 1 = never (recompute pass).
+ *   small_growth: when at most this many pixels of a region fail level A at
+ *                 3x3, one warp grows their windows with no block barriers:
+ *                 0 = default (32), -1 = never, 1..32.
+ *   select_lanes: lanes that share one median selection for windows of 7x7
+ *                 and more (they split the window's rows): 0 = default (up to
+ *                 4 at 7x7, 8 from 9x9), or 1, 2, 4, 8 as the cap.
+ *   batch_lag:    batches queue an image's Wiener tiles this many grids of
+ *                 tickets after its last median tile: 0 = default (6), 1..64.
+ *   batch_order:  0 = batches run in the caller's order (default); 1 = the
+ *                 largest images first.
+ * Applies to later launches in this process; results do not depend on it. */
 typedef struct {
     int region_h;
     int ctas_per_sm;
-    int reserved;
+    int plane;
+    int small_growth;
+    int select_lanes;
+    int batch_lag;
+    int batch_order;
 } hd_tuning;
 hd_status hd_set_tuning(const hd_tuning *t);
 hd_status hd_get_tuning(hd_tuning *t);

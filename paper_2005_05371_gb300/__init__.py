@@ -57,7 +57,12 @@ class hd_image(ctypes.Structure):
 
 
 class hd_tuning(ctypes.Structure):
-    _fields_ = [("region_h", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
+    _fields_ = [("region_h", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("plane", ctypes.c_int),
+                ("small_growth", ctypes.c_int), ("select_lanes", ctypes.c_int), ("batch_lag", ctypes.c_int),
+                ("batch_order", ctypes.c_int)]
+
+
+TUNING_FIELDS = ("region_h", "ctas_per_sm", "plane", "small_growth", "select_lanes", "batch_lag", "batch_order")
 
 
 class HDError(RuntimeError):
@@ -553,16 +558,22 @@ class BatchPipeline:
 
 
 # ----------------------------------------------------------------- tuning / errors
-def hd_set_tuning(region_h: int = 32, ctas_per_sm: int = 0):
-    """Rows per work item (multiple of 8 in [16, 128]) and CTAs per SM (0 = all that fit)."""
-    t = hd_tuning(region_h, ctas_per_sm, 0)
+def hd_set_tuning(region_h: int = 32, ctas_per_sm: int = 0, plane: int = 0, small_growth: int = 0,
+                  select_lanes: int = 0, batch_lag: int = 0, batch_order: int = 0):
+    """Work-item shape and scheduling knobs (see hd_tuning in the header):
+    rows per work item (multiple of 8 in [16, 128]), CTAs per SM (0 = all that
+    fit), statistics plane (0 = when there is room, 1 = never), one-warp growth
+    cut-over (0 = 32, -1 = never), lanes per median selection (0, 1, 2, 4, 8),
+    batch Wiener lag in grids (0 = 6) and batch order (0 = the caller's, 1 = largest first)."""
+    t = hd_tuning(region_h, ctas_per_sm, plane, small_growth, select_lanes, batch_lag, batch_order)
     _check(_lib.hd_set_tuning(ctypes.byref(t)), "hd_set_tuning")
 
 
-def hd_get_tuning() -> tuple[int, int]:
+def hd_get_tuning() -> tuple:
+    """The current knobs, in the order hd_set_tuning takes them."""
     t = hd_tuning()
     _check(_lib.hd_get_tuning(ctypes.byref(t)), "hd_get_tuning")
-    return t.region_h, t.ctas_per_sm
+    return tuple(getattr(t, f) for f in TUNING_FIELDS)
 
 
 def hd_set_spin_limit(polls: int = 0):

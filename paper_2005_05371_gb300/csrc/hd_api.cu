@@ -27,7 +27,7 @@ constexpr unsigned long long kSpinLimit = 8000000ull;   // polls of >= 256 ns: a
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 std::mutex g_tune_mu;
-hd_tuning g_tune = {32, 0, 0};
+hd_tuning g_tune = {32, 0, 0, 0, 0, 0, 0};
 unsigned long long g_spin_limit = kSpinLimit;
 
 }  // namespace
@@ -174,6 +174,8 @@ int halo_a(const ImgDesc &d) { return (d.mode == MODE_AMF || d.mode == MODE_HYBR
 hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t *smem)
 {
     lp.region_h = t.region_h;
+    lp.small_growth = t.small_growth == 0 ? 32 : (t.small_growth < 0 ? 0 : t.small_growth);
+    lp.select_lanes = t.select_lanes;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         lp.spin_limit = g_spin_limit;
@@ -207,7 +209,7 @@ hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, c
         ticket = static_cast<unsigned int *>(ws);
         ctl = reinterpret_cast<ImgCtl *>(static_cast<uint8_t *>(ws) + kTicketBytes);
         if (needs_fbuf) fbuf = static_cast<uint8_t *>(ws) + ctl_bytes();
-        if (ws_bytes >= need + plane_bytes(img->H, img->W))
+        if (t.plane == 0 && ws_bytes >= need + plane_bytes(img->H, img->W))
             plane = reinterpret_cast<float *>(static_cast<uint8_t *>(ws) + need);
     }
     LaunchParams lp;
@@ -289,7 +291,7 @@ struct BatchTables {
 
 // Wiener tiles of an image are queued this many grids of tickets after its
 // last median tile (see build_batch).
-constexpr int kBatchLagGrids = 3;
+constexpr int kBatchLagGrids = 6;
 
 // Grid of a batched launch with the current tuning (as finish_params sizes it).
 long long batch_grid(const BatchTables &bt)
@@ -334,7 +336,8 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
     // image's P1 tiles, and those were handed out `lag` tickets earlier:
     // with lag a few times the grid, they are done by the time it starts,
     // so the wait is rarely more than one poll.
-    const long long lag = (long long)kBatchLagGrids * batch_grid(bt);
+    const hd_tuning tn = current_tuning();
+    const long long lag = (long long)(tn.batch_lag ? tn.batch_lag : kBatchLagGrids) * batch_grid(bt);
     long long first = 0;
     auto push = [&](int img, int phase) {
         const ImgDesc &d = bt.descs[img];
@@ -342,10 +345,20 @@ hd_status build_batch(const hd_image *imgs, int n, void *ws, size_t ws_bytes, Ba
         bt.segs.push_back(Seg{img, phase, (int)first, items});
         first += items;
     };
+    // optionally the largest images first (the last images' Wiener tiles,
+    // which cannot lag behind enough median tiles, then wait only for small
+    // images' tails; measured no faster on the uneven 256-slice batch)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    if (tn.batch_order == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)bt.descs[a].H * bt.descs[a].W > (long long)bt.descs[b].H * bt.descs[b].W;
+        });
     std::vector<long long> p1_end(n, 0);
     std::vector<int> pending;           // images whose P2 is not placed yet, in order
     size_t head = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
         push(i, 1);
         p1_end[i] = first;
         if (mode_two_phase(bt.descs[i].mode)) pending.push_back(i);
@@ -1092,8 +1105,14 @@ hd_status hd_set_tuning(const hd_tuning *t)
 {
     if (!t) return HD_ERR_ARG;
     if (t->region_h < 16 || t->region_h > 128 || (t->region_h % 8) != 0) return HD_ERR_ARG;
-    if (t->reserved != 0) return HD_ERR_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 8) return HD_ERR_ARG;
+    if (t->plane < 0 || t->plane > 1) return HD_ERR_ARG;
+    if (t->small_growth < -1 || t->small_growth > 32) return HD_ERR_ARG;
+    if (t->select_lanes != 0 && t->select_lanes != 1 && t->select_lanes != 2 && t->select_lanes != 4 &&
+        t->select_lanes != 8)
+        return HD_ERR_ARG;
+    if (t->batch_lag < 0 || t->batch_lag > 64) return HD_ERR_ARG;
+    if (t->batch_order < 0 || t->batch_order > 1) return HD_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = *t;
     return HD_OK;

@@ -661,7 +661,8 @@ __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur,
 // sample values: c > (K*K-1)/2 puts the median at or below max{v <= t},
 // otherwise at or above min{v > t}.  Ends when lo == hi: the exact median.
 template <int K>
-__device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel, const u32 *st_mm)
+__device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel, const u32 *st_mm,
+                             int lanes_cap)
 {
     constexpr int R = K / 2, M0 = (K * K - 1) / 2;
     if (K == 5) {
@@ -672,7 +673,7 @@ __device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *se
         }
         return;
     }
-    constexpr int GMAX = K >= 9 ? 8 : 4;
+    const int GMAX = lanes_cap ? lanes_cap : (K >= 9 ? 8 : 4);
     int G = 1;
     while (G < GMAX && nsel * G * 2 <= kThreads) G *= 2;
     const int gid = threadIdx.x / G, gl = threadIdx.x & (G - 1), ngroups = kThreads / G;
@@ -720,6 +721,80 @@ __device__ void select_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *se
             }
         }
         if (valid && gl == 0) {
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            fs[r * FS + c] = (u16)lo;
+        }
+    }
+}
+
+// Medians of the K x K windows (K >= 7) of the nsel pixels on the selection
+// list, for values below 2^15.  G lanes per pixel (4 at 7x7, 8 from 9x9)
+// split the window's rows and keep their samples in registers, two to a
+// 32-bit word (a row's odd last sample, and rows past the window, are padded
+// with 0x7fff, which no threshold reaches).  Then bisection on the value:
+// the median is the smallest t with c(t) = #{v <= t} > (K*K-1)/2, so c(t) >
+// (K*K-1)/2 puts it at or below t, otherwise above.  The bracket starts
+// strictly inside (zmin, zmax) (level A holds) and halves every pass:
+// ceil(log2(zmax - zmin - 1)) passes.  One word counts both of its samples:
+// with both halves below 2^15, ((0x8000 | t) * 0x10001) - w has bit 15 (31)
+// set exactly where its low (high) sample is <= t, and no borrow crosses
+// from one half into the other.
+template <int K>
+__device__ void select_level_packed(const Geo &g, const u16 *gs, u16 *fs, const u16 *sel_top, int nsel,
+                                    const u32 *st_mm)
+{
+    constexpr int R = K / 2, M0 = (K * K - 1) / 2;
+    constexpr int G = K >= 9 ? 8 : 4;
+    constexpr int ROWS = (K + G - 1) / G;      // rows per lane
+    constexpr int WPR = (K + 1) / 2;           // words per row
+    const int gid = threadIdx.x / G, gl = threadIdx.x & (G - 1);
+    constexpr int ngroups = kThreads / G;
+    const int rounds = (nsel + ngroups - 1) / ngroups;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int e = rd * ngroups + gid;
+        u32 ent = 0, lo = 1, hi = 0;
+        u32 w[ROWS * WPR];
+#pragma unroll
+        for (int i = 0; i < ROWS * WPR; ++i) w[i] = 0x7fff7fffu;
+        if (e < nsel) {
+            ent = *(sel_top - e);
+            const int r = (int)(ent >> 6), c = (int)(ent & 63u);
+            const u16 *ctr = gs + (r + g.Ra) * g.GS + (c + g.Ra + g.pa);
+            const u32 mm = st_mm[ent];
+            lo = (mm & 0xffffu) + 1u;
+            hi = (mm >> 16) - 1u;
+#pragma unroll
+            for (int j = 0; j < ROWS; ++j) {
+                const int dy = gl - R + j * G;
+                const u16 *row = ctr + dy * g.GS;
+#pragma unroll
+                for (int q = 0; q < WPR; ++q) {
+                    const int dx = 2 * q - R;
+                    u32 a = 0x7fffu, b = 0x7fffu;
+                    if (dy <= R) {
+                        a = row[dx];
+                        if (dx + 1 <= R) b = row[dx + 1];
+                    }
+                    w[j * WPR + q] = a | (b << 16);
+                }
+            }
+        }
+        // every lane of the warp runs the same number of passes (shuffles)
+        while (__any_sync(FULL, lo < hi)) {
+            const u32 t = (lo + hi) >> 1;
+            const u32 T = (0x8000u | t) * 0x10001u;
+            u32 cnt = 0;
+#pragma unroll
+            for (int i = 0; i < ROWS * WPR; ++i) cnt += ((T - w[i]) >> 15) & 0x10001u;
+            cnt = (cnt & 0xffffu) + (cnt >> 16);
+#pragma unroll
+            for (int m = 1; m < G; m <<= 1) cnt += __shfl_xor_sync(FULL, cnt, m);
+            if (lo < hi) {
+                if (cnt > (u32)M0) hi = t;
+                else lo = t + 1;
+            }
+        }
+        if (e < nsel && gl == 0) {
             const int r = (int)(ent >> 6), c = (int)(ent & 63u);
             fs[r * FS + c] = (u16)lo;
         }
@@ -824,12 +899,15 @@ __device__ void grow_small(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *f
 }
 
 // Windows k = 5..Smax for the pixels that failed level A at k = 3.
+template <bool PACK>
 __device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl0, u16 *wl1, int *cnt,
-                         int cap, u32 *st_mm, u16 *st_c)
+                         int cap, u32 *st_mm, u16 *st_c, int small_growth, int lanes_cap)
 {
     const int n0 = cnt[0];
-    if (n0 <= 32) {
+    HD_STAMP_INIT();
+    if (n0 <= small_growth) {
         if (n0 > 0 && threadIdx.x < 32) grow_small(d, g, gs, fs, wl0, n0);
+        HD_STAMP(11);
         return;
     }
     const bool keep = d.unresolved != 0;
@@ -854,18 +932,31 @@ __device__ void amf_grow(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs,
             break;
         }
         __syncthreads();
+        HD_STAMP(8);
         const int nsel = cnt[2];
         if (nsel > 0) {
             const u16 *top = nxt + cap - 1;
-            switch (k) {
-            case 5: select_level<5>(g, gs, fs, top, nsel, st_mm); break;
-            case 7: select_level<7>(g, gs, fs, top, nsel, st_mm); break;
-            case 9: select_level<9>(g, gs, fs, top, nsel, st_mm); break;
-            case 11: select_level<11>(g, gs, fs, top, nsel, st_mm); break;
-            case 13: select_level<13>(g, gs, fs, top, nsel, st_mm); break;
-            default: select_level<15>(g, gs, fs, top, nsel, st_mm); break;
+            if (PACK) {
+                switch (k) {
+                case 5: select_level<5>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                case 7: select_level_packed<7>(g, gs, fs, top, nsel, st_mm); break;
+                case 9: select_level_packed<9>(g, gs, fs, top, nsel, st_mm); break;
+                case 11: select_level_packed<11>(g, gs, fs, top, nsel, st_mm); break;
+                case 13: select_level_packed<13>(g, gs, fs, top, nsel, st_mm); break;
+                default: select_level_packed<15>(g, gs, fs, top, nsel, st_mm); break;
+                }
+            } else {
+                switch (k) {
+                case 5: select_level<5>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                case 7: select_level<7>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                case 9: select_level<9>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                case 11: select_level<11>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                case 13: select_level<13>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                default: select_level<15>(g, gs, fs, top, nsel, st_mm, lanes_cap); break;
+                }
             }
             __syncthreads();
+            HD_STAMP(k == 5 ? 9 : 10);
         }
         u16 *t = cur; cur = nxt; nxt = t;
         ci ^= 1;
@@ -1549,7 +1640,9 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         else amf3_scalar(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
         __syncthreads();
         HD_STAMP(1);
-        if (d.smax > 3) amf_grow(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW, vw.st_mm, vw.st_c);
+        if (d.smax > 3)
+            amf_grow<PACK>(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW, vw.st_mm, vw.st_c,
+                           lp.small_growth, lp.select_lanes);
         if (g.Rw > 0 && d.border_zero) {
             // zero-border Wiener: samples outside the image read 0 (after every
             // growth write: the short-worklist path ends without a barrier)

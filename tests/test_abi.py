@@ -114,11 +114,15 @@ def test_workspace_sizes():
 def test_tuning_validation():
     old = hd.hd_get_tuning()
     try:
-        for bad in ((8, 0), (20, 0), (136, 0), (32, 9), (32, -1)):
+        for bad in ((8, 0), (20, 0), (136, 0), (32, 9), (32, -1), (32, 0, 2), (32, 0, -1), (32, 0, 0, 33),
+                    (32, 0, 0, -2), (32, 0, 0, 0, 3), (32, 0, 0, 0, 16), (32, 0, 0, 0, 0, 65), (32, 0, 0, 0, 0, -1),
+                    (32, 0, 0, 0, 0, 0, 2)):
             with pytest.raises(hd.HDError):
                 hd.hd_set_tuning(*bad)
         hd.hd_set_tuning(64, 2)
-        assert hd.hd_get_tuning() == (64, 2)
+        assert hd.hd_get_tuning() == (64, 2, 0, 0, 0, 0, 0)
+        hd.hd_set_tuning(48, 3, 1, -1, 8, 5, 1)
+        assert hd.hd_get_tuning() == (48, 3, 1, -1, 8, 5, 1)
     finally:
         hd.hd_set_tuning(*old)
 
