@@ -233,6 +233,58 @@ hd_status hybrid_host_workspace_size(int H, int W, int dtype, const hd_params *p
 #define HD_STATIC_SCRATCH_BYTES (36u * 1024u * 1024u)
 hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
 
+/* ---------------------------------------------------------------- image parts
+ * One image split across GPUs by row strips, one part per GPU: the paper's
+ * partitioned parallel step (Algorithm 1, step 6, parfor over the image's
+ * sub-images; Fig. 5), here with whole-image results.  Each part computes
+ * the output rows it owns exactly as hybrid_denoise does for the whole image:
+ * it holds its own rows plus the halo rows that their windows read (copied
+ * from the neighbouring parts first), and the one image-wide quantity, the
+ * noise variance (mean local variance, Algorithm 1, step 4d), comes from four
+ * exact integer sums that the caller adds over all parts between the two
+ * calls (an all-reduce).  The reassembled image is bit-identical to
+ * hybrid_denoise of the whole image.
+ *   H, W:     the WHOLE image.
+ *   buf_row0, buf_rows: the rows src holds, [buf_row0, buf_row0 + buf_rows).
+ *             They must include [max(0, own_row0 - h), min(H, own_row0 +
+ *             own_rows + h)), h = hd_part_halo_rows() = smax/2 + wiener_w/2.
+ *   own_row0, own_rows: the rows this part owns and writes.
+ *   src:      device, buf_rows rows of src_pitch bytes (the noisy image).
+ *   dst:      device, own_rows rows of dst_pitch bytes: dst row 0 is image
+ *             row own_row0.  Must not overlap src (hybrid_part_apply).
+ *   p:        as for hybrid_denoise; noise_var must be < 0 (estimated: with a
+ *             known noise variance there is nothing to exchange; run
+ *             hybrid_denoise on each part's buffer and keep its own rows).
+ * hybrid_part_stats: the median and the local statistics of the own rows
+ *   (one persistent launch); writes the part's four sums to sums_out
+ *   (device, 8-byte aligned, 4 x uint64: the low and high 32-bit halves of
+ *   A = sum S1^2 and of B = sum M(q) f^2, accumulated in 64-bit words).
+ * The caller adds the four words over all parts, word by word (uint64 or
+ *   int64 sum; exact for fewer than 2^32 tiles in all), e.g. with one NCCL
+ *   all-reduce, and passes the result to
+ * hybrid_part_apply: the Wiener output of the own rows into dst (one
+ *   persistent launch), with nu2 from the summed words.
+ * workspace: device, 256-byte aligned, >= hybrid_part_workspace_size(); the
+ *   same workspace for both calls of a part (the median and statistics planes
+ *   live in it between them).  hybrid_part_stats clears what it needs. */
+typedef struct {
+    const void *src;
+    size_t src_pitch;
+    void *dst;
+    size_t dst_pitch;
+    int H, W;
+    int buf_row0, buf_rows;
+    int own_row0, own_rows;
+    int dtype;
+    hd_params p;
+} hd_part;
+hd_status hd_part_halo_rows(const hd_params *p, int *rows);
+hd_status hybrid_part_workspace_size(const hd_part *part, size_t *bytes);
+hd_status hybrid_part_stats(const hd_part *part, void *workspace, size_t ws_bytes, unsigned long long *sums_out,
+                            hd_stream_t stream);
+hd_status hybrid_part_apply(const hd_part *part, const unsigned long long *sums, void *workspace, size_t ws_bytes,
+                            hd_stream_t stream);
+
 /* ---------------------------------------------------------------- reference
  * Noise variance of an image against a clean reference (Algorithm 1, step 4d
  * hands the original image to the Wiener stage; this reads it as the source

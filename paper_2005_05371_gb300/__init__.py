@@ -42,6 +42,7 @@ EXPORTS = [
     "hd_host_pipeline_wait", "hd_host_pipeline_destroy",
     "hd_batch_pipeline_workspace_size", "hd_batch_pipeline_create", "hd_batch_pipeline_submit",
     "hd_batch_pipeline_wait", "hd_batch_pipeline_destroy",
+    "hd_part_halo_rows", "hybrid_part_workspace_size", "hybrid_part_stats", "hybrid_part_apply",
 ]
 
 
@@ -54,6 +55,13 @@ class hd_image(ctypes.Structure):
     _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("src_pitch", ctypes.c_size_t), ("dst_pitch", ctypes.c_size_t), ("dtype", ctypes.c_int),
                 ("p", hd_params), ("noise_var_out", ctypes.c_void_p), ("y_out", ctypes.c_void_p)]
+
+
+class hd_part(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("src_pitch", ctypes.c_size_t), ("dst", ctypes.c_void_p),
+                ("dst_pitch", ctypes.c_size_t), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("buf_row0", ctypes.c_int), ("buf_rows", ctypes.c_int), ("own_row0", ctypes.c_int),
+                ("own_rows", ctypes.c_int), ("dtype", ctypes.c_int), ("p", hd_params)]
 
 
 class hd_tuning(ctypes.Structure):
@@ -112,6 +120,10 @@ def _load() -> ctypes.CDLL:
                                       ctypes.POINTER(S)], I),
         "hd_batch_pipeline_wait": ([P], I),
         "hd_batch_pipeline_destroy": ([P], I),
+        "hd_part_halo_rows": ([par_p, ctypes.POINTER(I)], I),
+        "hybrid_part_workspace_size": ([ctypes.POINTER(hd_part), ctypes.POINTER(S)], I),
+        "hybrid_part_stats": ([ctypes.POINTER(hd_part), P, S, P, P], I),
+        "hybrid_part_apply": ([ctypes.POINTER(hd_part), P, P, S, P], I),
         "hybrid_strips_workspace_size": ([I, I, I, par_p, I, ctypes.POINTER(S)], I),
         "contrast_workspace_size": ([I, I, I, par_p, ctypes.POINTER(S)], I),
         "hd_status_str": ([I], ctypes.c_char_p),
@@ -555,6 +567,44 @@ class BatchPipeline:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- image parts
+def part_halo_rows(params: Params, dtype_code: int = HD_U8) -> int:
+    """Rows of halo a part needs above and below its own rows: smax/2 + w/2."""
+    n = ctypes.c_int()
+    _check(_lib.hd_part_halo_rows(ctypes.byref(params.to_c(dtype_code)), ctypes.byref(n)), "hd_part_halo_rows")
+    return n.value
+
+
+def make_part(buf, dst, H: int, W: int, buf_row0: int, own_row0: int, own_rows: int, params: Params) -> hd_part:
+    """hd_part for a buffer of rows [buf_row0, buf_row0 + len(buf)) of an H x W
+    image and the part's own rows [own_row0, own_row0 + own_rows) (dst: their
+    output, or None for the statistics call)."""
+    code = _dtype_code(buf)
+    return hd_part(buf.data_ptr(), _pitch(buf), dst.data_ptr() if dst is not None else None,
+                   _pitch(dst) if dst is not None else 0, int(H), int(W), int(buf_row0), int(buf.shape[0]),
+                   int(own_row0), int(own_rows), code, params.to_c(code))
+
+
+def hybrid_part_workspace_size(part: hd_part) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.hybrid_part_workspace_size(ctypes.byref(part), ctypes.byref(n)), "hybrid_part_workspace_size")
+    return n.value
+
+
+def hybrid_part_stats(part: hd_part, workspace, sums_out, stream=None):
+    """Median and local statistics of a part's own rows; its four sums into
+    ``sums_out`` (a 4-element int64 CUDA tensor)."""
+    _check(_lib.hybrid_part_stats(ctypes.byref(part), _ws_ptr(workspace), _ws_len(workspace), sums_out.data_ptr(),
+                                  _stream_ptr(stream)), "hybrid_part_stats")
+    return sums_out
+
+
+def hybrid_part_apply(part: hd_part, sums, workspace, stream=None):
+    """Wiener output of a part's own rows, with the sums of all parts."""
+    _check(_lib.hybrid_part_apply(ctypes.byref(part), sums.data_ptr(), _ws_ptr(workspace), _ws_len(workspace),
+                                  _stream_ptr(stream)), "hybrid_part_apply")
 
 
 # ----------------------------------------------------------------- tuning / errors

@@ -158,6 +158,10 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     d.tiles_x = (img->W + TW - 1) / TW;
     d.tiles_y = (img->H + TH - 1) / TH;
     d.p2_items = plane ? 0 : d.tiles_x * d.tiles_y;
+    d.Hg = img->H;
+    d.gy_off = 0;
+    d.own0 = 0;
+    d.own1 = img->H;
     return d;
 }
 
@@ -1099,6 +1103,190 @@ hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pl)
     if (!pl) return HD_ERR_ARG;
     batch_pipe_release(pl);
     return HD_OK;
+}
+
+// ---------------------------------------------------------------- image parts
+// One image split by row strips, one part per GPU.  A part's workspace:
+// [queue counters + control block][median plane of the buffer rows]
+// [statistics plane of the buffer rows, 16 bytes to spare].
+static size_t part_plane_bytes(const hd_part *pt)
+{
+    return round_up((size_t)pt->buf_rows * (size_t)pt->W * 2 * sizeof(float) + 16, kAlign);
+}
+
+static hd_status check_part(const hd_part *pt, bool need_dst)
+{
+    if (!pt) return HD_ERR_ARG;
+    if (pt->dtype != HD_U8 && pt->dtype != HD_U16) return HD_ERR_DTYPE;
+    if (pt->dtype == HD_U8 && pt->p.bits != 8) return HD_ERR_DTYPE;
+    if (pt->dtype == HD_U16 && (pt->p.bits < 1 || pt->p.bits > 16)) return HD_ERR_DTYPE;
+    if (pt->H < 1 || pt->W < 1) return HD_ERR_ARG;
+    if (pt->H > HD_DIM_MAX || pt->W > HD_DIM_MAX) return HD_ERR_OVERFLOW;
+    const int s = pt->p.smax, w = pt->p.wiener_w;
+    if (s < 3 || s > HD_SMAX_MAX || (s & 1) == 0) return HD_ERR_SMAX;
+    if (w < 1 || w > HD_WIENER_W_MAX || (w & 1) == 0) return HD_ERR_WINDOW;
+    if (pt->p.unresolved != HD_UNRESOLVED_ZMED && pt->p.unresolved != HD_UNRESOLVED_KEEP) return HD_ERR_ARG;
+    if (pt->p.border != HD_BORDER_SYMMETRIC && pt->p.border != HD_BORDER_ZERO) return HD_ERR_ARG;
+    // only the estimated noise variance needs the exchange of sums
+    if (!(pt->p.noise_var < 0.0)) return HD_ERR_ARG;
+    // rows: the part's own rows inside its buffer, the buffer inside the image,
+    // and the buffer holding every halo row the own rows' windows read
+    const int h = s / 2 + w / 2;
+    if (pt->buf_row0 < 0 || pt->buf_rows < 1 || pt->buf_row0 + pt->buf_rows > pt->H) return HD_ERR_ARG;
+    if (pt->own_rows < 1 || pt->own_row0 < pt->buf_row0 ||
+        pt->own_row0 + pt->own_rows > pt->buf_row0 + pt->buf_rows)
+        return HD_ERR_ARG;
+    if (pt->buf_row0 > std::max(0, pt->own_row0 - h)) return HD_ERR_ARG;
+    if (pt->buf_row0 + pt->buf_rows < std::min(pt->H, pt->own_row0 + pt->own_rows + h)) return HD_ERR_ARG;
+    const size_t es = (size_t)elem_size(pt->dtype), row = (size_t)pt->W * es;
+    if (!pt->src || pt->src_pitch < row) return HD_ERR_ARG;
+    if (es == 2 && (((uintptr_t)pt->src | pt->src_pitch) & 1)) return HD_ERR_ARG;
+    if (need_dst) {
+        if (!pt->dst || pt->dst_pitch < row) return HD_ERR_ARG;
+        if (es == 2 && (((uintptr_t)pt->dst | pt->dst_pitch) & 1)) return HD_ERR_ARG;
+        const uintptr_t s0 = (uintptr_t)pt->src, s1 = s0 + (size_t)(pt->buf_rows - 1) * pt->src_pitch + row;
+        const uintptr_t d0 = (uintptr_t)pt->dst, d1 = d0 + (size_t)(pt->own_rows - 1) * pt->dst_pitch + row;
+        if (s0 < d1 && d0 < s1) return HD_ERR_ARG;
+    }
+    return HD_OK;
+}
+
+// The descriptor of a part: the buffer as the image, the own rows as the
+// tiled and applied range, the whole image's rows for M(q) and the noise
+// variance's denominator.
+static ImgDesc part_desc(const hd_part *pt, const hd_tuning &t, uint8_t *ws)
+{
+    hd_image img;
+    std::memset(&img, 0, sizeof(img));
+    img.src = pt->src;
+    img.dst = pt->dst;
+    img.H = pt->buf_rows;
+    img.W = pt->W;
+    img.src_pitch = pt->src_pitch;
+    img.dst_pitch = pt->dst_pitch;
+    img.dtype = pt->dtype;
+    img.p = pt->p;
+    ImgCtl *ctl = reinterpret_cast<ImgCtl *>(ws + kTicketBytes);
+    uint8_t *fbuf = ws + ctl_bytes();
+    const size_t fb = round_up((size_t)pt->buf_rows * f_pitch_of(pt->W, pt->dtype), kAlign);
+    const int own0 = pt->own_row0 - pt->buf_row0;
+    // the plane base sits 8 bytes past a 16-byte boundary when the first owned
+    // pixel's index is odd, so that pixel's (mu, s2) pair is 16-byte aligned
+    const size_t shift = ((size_t)own0 * (size_t)pt->W) & 1 ? 8 : 0;
+    float *plane = reinterpret_cast<float *>(ws + ctl_bytes() + fb + shift);
+    ImgDesc d = make_desc(&img, MODE_HYBRID_EST, t, ctl, fbuf, plane);
+    d.Hg = pt->H;
+    d.gy_off = pt->buf_row0;
+    d.own0 = own0;
+    d.own1 = own0 + pt->own_rows;
+    // output row y of the buffer goes to row y - own0 of the part's own rows
+    d.dst = static_cast<uint8_t *>(pt->dst) - (ptrdiff_t)own0 * (ptrdiff_t)pt->dst_pitch;
+    {
+        const double nw = (double)pt->p.wiener_w * (double)pt->p.wiener_w;
+        d.inv_den = 1.0 / (nw * nw * (double)pt->H * (double)pt->W);
+    }
+    const int rw = pt->p.wiener_w / 2;
+    const int TH = t.region_h - 2 * rw;
+    d.tiles_y = (pt->own_rows + TH - 1) / TH;
+    d.p2_items = 0;
+    return d;
+}
+
+static hd_status part_launch(const hd_part *pt, void *ws, size_t ws_bytes, int phase, cudaStream_t s)
+{
+    size_t need = 0;
+    hd_status st = hybrid_part_workspace_size(pt, &need);
+    if (st != HD_OK) return st;
+    if (!ws || ((uintptr_t)ws % kAlign) || ws_bytes < need) return HD_ERR_WORKSPACE;
+    const hd_tuning t = current_tuning();
+    uint8_t *base = static_cast<uint8_t *>(ws);
+    LaunchParams lp;
+    std::memset(&lp, 0, sizeof(lp));
+    lp.one = part_desc(pt, t, base);
+    const int tiles = lp.one.tiles_x * lp.one.tiles_y;
+    lp.ticket = reinterpret_cast<unsigned int *>(base);
+    lp.ctl_reset = lp.one.ctl;
+    lp.ra_max = pt->p.smax / 2;
+    lp.wide = image_wide(lp.one);
+    if (phase == 1) {
+        // the median and statistics tiles; the sums stay in the control block
+        lp.oneseg[0] = Seg{0, 1, 0, tiles};
+        lp.nsegs = 1;
+        lp.total_items = tiles;
+        lp.nctl = 0;
+    } else {
+        // the apply of the own rows from the plane; the last CTA clears the
+        // control block for the part's next call
+        lp.oneseg[0] = Seg{0, 1, 0, 0};
+        lp.nsegs = 1;
+        lp.total_items = 0;
+        lp.p2_plane = 1;
+        lp.nctl = 1;
+    }
+    int grid = 0;
+    size_t smem = 0;
+    st = finish_params(lp, t, &grid, &smem);
+    if (st != HD_OK) return st;
+    if (launch_persistent(lp, grid, smem, (void *)s) != 0) return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+hd_status hd_part_halo_rows(const hd_params *p, int *rows)
+{
+    if (!p || !rows) return HD_ERR_ARG;
+    if (p->smax < 3 || p->smax > HD_SMAX_MAX || (p->smax & 1) == 0) return HD_ERR_SMAX;
+    if (p->wiener_w < 1 || p->wiener_w > HD_WIENER_W_MAX || (p->wiener_w & 1) == 0) return HD_ERR_WINDOW;
+    *rows = p->smax / 2 + p->wiener_w / 2;
+    return HD_OK;
+}
+
+hd_status hybrid_part_workspace_size(const hd_part *pt, size_t *bytes)
+{
+    if (!bytes) return HD_ERR_ARG;
+    hd_status st = check_part(pt, false);
+    if (st != HD_OK) return st;
+    *bytes = ctl_bytes() + round_up((size_t)pt->buf_rows * f_pitch_of(pt->W, pt->dtype), kAlign) +
+             part_plane_bytes(pt);
+    return HD_OK;
+}
+
+hd_status hybrid_part_stats(const hd_part *pt, void *workspace, size_t ws_bytes, unsigned long long *sums_out,
+                            hd_stream_t stream)
+{
+    hd_status st = check_part(pt, false);
+    if (st != HD_OK) return st;
+    if (!sums_out || ((uintptr_t)sums_out & 7)) return HD_ERR_ARG;
+    size_t need = 0;
+    hybrid_part_workspace_size(pt, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < need) return HD_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the part's sums start from zero
+    if (cudaMemsetAsync(workspace, 0, ctl_bytes(), s) != cudaSuccess) return HD_ERR_CUDA;
+    st = part_launch(pt, workspace, ws_bytes, 1, s);
+    if (st != HD_OK) return st;
+    const ImgCtl *ctl = reinterpret_cast<const ImgCtl *>(static_cast<uint8_t *>(workspace) + kTicketBytes);
+    if (cudaMemcpyAsync(sums_out, &ctl->A_lo32, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    return HD_OK;
+}
+
+hd_status hybrid_part_apply(const hd_part *pt, const unsigned long long *sums, void *workspace, size_t ws_bytes,
+                            hd_stream_t stream)
+{
+    hd_status st = check_part(pt, true);
+    if (st != HD_OK) return st;
+    if (!sums || ((uintptr_t)sums & 7)) return HD_ERR_ARG;
+    size_t need = 0;
+    hybrid_part_workspace_size(pt, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) || ws_bytes < need) return HD_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    ImgCtl *ctl = reinterpret_cast<ImgCtl *>(static_cast<uint8_t *>(workspace) + kTicketBytes);
+    // the whole image's sums replace the part's own
+    if (cudaMemcpyAsync(&ctl->A_lo32, sums, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return HD_ERR_CUDA;
+    return part_launch(pt, workspace, ws_bytes, 2, s);
 }
 
 hd_status hd_set_tuning(const hd_tuning *t)

@@ -62,6 +62,11 @@ struct ImgDesc {
     float *plane;             // optional (estimated noise variance): per output pixel the
                               // binary32 pair (mu, s2) left by phase 1, row-major, W pairs a row;
                               // nullptr: phase 2 recomputes the sums from the f region
+    // A part of a larger image (one image split by row strips): the buffers
+    // hold rows [gy_off, gy_off + H) of an image of Hg rows, and the part owns
+    // (tiles, statistics and output) local rows [own0, own1).  A whole image:
+    // Hg = H, gy_off = 0, own0 = 0, own1 = H.
+    int Hg, gy_off, own0, own1;
 };
 
 // A run of consecutive tickets belonging to one (image, phase).

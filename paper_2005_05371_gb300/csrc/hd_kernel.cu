@@ -1151,11 +1151,12 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     constexpr bool with_plane = PLANE;
     hsums<NARROW>(g, fs, H1, h2p, w, with_plane);
     const bool zero = d.border_zero != 0;
-    const bool interior = !zero && g.y0 >= g.Rw && g.y0 + g.th <= d.H - g.Rw && g.x0 >= g.Rw &&
+    const int gy0 = g.y0 + d.gy_off;       // the tile's first row in the whole image
+    const bool interior = !zero && gy0 >= g.Rw && gy0 + g.th <= d.Hg - g.Rw && g.x0 >= g.Rw &&
                           g.x0 + g.tw <= d.W - g.Rw;
     if (!interior) {
         for (int i = threadIdx.x; i < g.th + g.tw; i += kThreads) {
-            if (i < g.th) bs.my[i] = window_multiplicity(g.y0 + i, d.H, g.Rw, zero);
+            if (i < g.th) bs.my[i] = window_multiplicity(gy0 + i, d.Hg, g.Rw, zero);
             else bs.mx[i - g.th] = window_multiplicity(g.x0 + i - g.th, d.W, g.Rw, zero);
         }
     }
@@ -1190,7 +1191,8 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         }
         float2 *pp = with_plane ? reinterpret_cast<float2 *>(d.plane) + (long long)(g.y0 + j0) * d.W + g.x0 + x
                                 : nullptr;
-        const bool pair16 = two && ((d.W | g.x0) & 1) == 0;      // (mu, s2) pairs land 16-byte aligned
+        const bool pair16 = two && ((d.W | g.x0) & 1) == 0 &&
+                            (reinterpret_cast<uintptr_t>(d.plane) & 15) == 0;   // (mu, s2) pairs land 16-byte aligned
         for (int j = j0; j < j1; ++j) {
             const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
             const u32 fa = fp & 0xffffu, fb = fp >> 16;
@@ -1217,7 +1219,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
                 }
                 const float mua = __fmul_rn(__uint2float_rn(sa), inv_n), s2a = __fmul_rn(da, inv_n2);
                 const float mub = __fmul_rn(__uint2float_rn(sb), inv_n), s2b = __fmul_rn(db, inv_n2);
-                if (pair16) {
+                if (pair16 || (two && (reinterpret_cast<uintptr_t>(pp) & 15) == 0)) {
                     *reinterpret_cast<float4 *>(pp) = make_float4(mua, s2a, mub, s2b);
                 } else {
                     pp[0] = make_float2(mua, s2a);
@@ -1358,10 +1360,11 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, u32 bytes,
                  : "memory");
 }
 
-// Thread 0: stage pixels [q0, q0 + n) of image d (q0 even) into stage s.
+// Thread 0: stage pixels [q0, q0 + n) of image d into stage s; q0 - own0 W is
+// even and the plane base puts that pixel's pair on a 16-byte boundary.
 // Every address and size is a multiple of 16 bytes and stays inside its
-// buffer: the plane is allocated in whole 256-byte blocks, f rows have a
-// 16-byte-multiple pitch.
+// buffer: the plane is allocated in whole 256-byte blocks with 16 bytes to
+// spare, f rows have a 16-byte-multiple pitch.
 __device__ void p2_issue(const ImgDesc &d, u32 q0, u32 n, int s, unsigned char *stages, P2Stage *st, u64 *full)
 {
     // row of q0: a binary32 estimate (off by at most one) corrected exactly
@@ -1686,7 +1689,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     if (threadIdx.x == 0) {
         if (!est || bs.nu2_of != d.ctl) {
             const u64 n = (u64)d.w * (u64)d.w;
-            const double nu2 = est ? noise_variance(d.ctl, n, d.H, d.W, d.inv_den) : d.noise_var;
+            const double nu2 = est ? noise_variance(d.ctl, n, d.Hg, d.W, d.inv_den) : d.noise_var;
             bs.nu2 = nu2;
             bs.nu2f = __double2float_rn(nu2);
             bs.nu2_of = est ? d.ctl : nullptr;
@@ -1708,9 +1711,12 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
     // the plane and f rows were written by other CTAs (generic stores, made
     // visible by the wait); the bulk copies read them through the async proxy
     if (threadIdx.x < kStages) asm volatile("fence.proxy.async.global;" ::: "memory");
-    const u64 HW = (u64)d.H * (u64)d.W;
-    const u64 per = ((HW + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
-    const u32 pb = (u32)min(HW, 2 * per * blockIdx.x), pe = (u32)min(HW, 2 * per * (blockIdx.x + 1));
+    // the owned pixels [P0, P1) (the whole image unless it is a part), in
+    // shares starting P0 + an even offset: with the plane base placed so that
+    // pixel P0's pair is 16-byte aligned, every unit's pairs are too
+    const u64 P0 = (u64)d.own0 * (u64)d.W, NP = (u64)(d.own1 - d.own0) * (u64)d.W;
+    const u64 per = ((NP + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
+    const u32 pb = (u32)(P0 + min(NP, 2 * per * blockIdx.x)), pe = (u32)(P0 + min(NP, 2 * per * (blockIdx.x + 1)));
     // K units of one even size (the last one takes the remainder): every unit
     // starts inside the share
     const u32 S = pe - pb, K0 = (S + kUnitPx - 1) / kUnitPx;
@@ -1732,7 +1738,7 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
         }
     }
     if (threadIdx.x == 32) {
-        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.H, d.W, d.inv_den);
+        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.Hg, d.W, d.inv_den);
         bs.nu2 = nu2;
         bs.nu2f = __double2float_rn(nu2);
         if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
@@ -1791,9 +1797,9 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
     g.GS = g_stride(g.Ra);
     const int tyi = tile / d.tiles_x, txi = tile - tyi * d.tiles_x;
     g.x0 = txi * TW;
-    g.y0 = tyi * TH;
+    g.y0 = d.own0 + tyi * TH;
     g.tw = min(TW, d.W - g.x0);
-    g.th = min(TH, d.H - g.y0);
+    g.th = min(TH, d.own1 - g.y0);
     g.ncol = g.Lm + g.tw + g.Rw;
     g.nrow = g.th + 2 * g.Rw;
     g.gfx = g.x0 - g.Lm;

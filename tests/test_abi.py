@@ -229,6 +229,55 @@ def test_batch_pipeline_argument_checks():
     assert lib.hd_batch_pipeline_destroy(None) == hd.HD_ERR_ARG
 
 
+def test_part_argument_checks():
+    lib = hd._lib
+    S = ctypes.c_size_t
+
+    def part(**kw):
+        a = dict(src=0x100000, src_pitch=64, dst=0x900000, dst_pitch=64, H=100, W=64, buf_row0=20, buf_rows=40,
+                 own_row0=25, own_rows=30, dtype=hd.HD_U8, smax=7, w=5, nv=-1.0, border=0, unres=0, bits=8)
+        a.update(kw)
+        p = hd.hd_params(a["smax"], a["w"], a["nv"], a["border"], a["unres"], a["bits"])
+        return hd.hd_part(a["src"], a["src_pitch"], a["dst"], a["dst_pitch"], a["H"], a["W"], a["buf_row0"],
+                          a["buf_rows"], a["own_row0"], a["own_rows"], a["dtype"], p)
+
+    n = S()
+    halo = ctypes.c_int()
+    assert lib.hd_part_halo_rows(ctypes.byref(hd.Params(7, 5).to_c(hd.HD_U8)), ctypes.byref(halo)) == hd.HD_OK
+    assert halo.value == 5
+    assert lib.hd_part_halo_rows(ctypes.byref(hd.Params(6, 5).to_c(hd.HD_U8)), ctypes.byref(halo)) == hd.HD_ERR_SMAX
+    ok = part()
+    assert lib.hybrid_part_workspace_size(ctypes.byref(ok), ctypes.byref(n)) == hd.HD_OK
+    assert n.value >= 40 * 64 * 8
+    cases = [
+        (dict(buf_row0=21), hd.HD_ERR_ARG),              # buffer misses a halo row above
+        (dict(buf_rows=39), hd.HD_ERR_ARG),              # ... and below
+        (dict(own_row0=19), hd.HD_ERR_ARG),              # own rows outside the buffer
+        (dict(buf_row0=70, own_row0=75, buf_rows=31), hd.HD_ERR_ARG),   # buffer beyond the image
+        (dict(own_rows=0), hd.HD_ERR_ARG),
+        (dict(nv=5.0), hd.HD_ERR_ARG),                   # a known noise variance needs no split
+        (dict(smax=8), hd.HD_ERR_SMAX),
+        (dict(w=4), hd.HD_ERR_WINDOW),
+        (dict(dtype=hd.HD_U16, bits=12, src=0x100001, src_pitch=128, dst_pitch=128), hd.HD_ERR_ARG),
+        (dict(bits=12), hd.HD_ERR_DTYPE),
+        (dict(src_pitch=63), hd.HD_ERR_ARG),
+        (dict(H=70000), hd.HD_ERR_OVERFLOW),
+    ]
+    for kw, want in cases:
+        got = lib.hybrid_part_workspace_size(ctypes.byref(part(**kw)), ctypes.byref(n))
+        assert got == want, (kw, got, want)
+    # the buffer may start at row 0 when the halo would reach above the image
+    assert lib.hybrid_part_workspace_size(ctypes.byref(part(buf_row0=0, own_row0=3, buf_rows=38)),
+                                          ctypes.byref(n)) == hd.HD_OK
+    sums = 0x3000
+    assert lib.hybrid_part_stats(ctypes.byref(ok), 0x10000, 0, sums, None) == hd.HD_ERR_WORKSPACE
+    assert lib.hybrid_part_stats(ctypes.byref(ok), 0x10000, 1 << 30, 0x3004, None) == hd.HD_ERR_ARG
+    assert lib.hybrid_part_apply(ctypes.byref(part(dst=0)), sums, 0x10000, 1 << 30, None) == hd.HD_ERR_ARG
+    assert lib.hybrid_part_apply(ctypes.byref(part(dst=0x100000 + 64 * 10)), sums, 0x10000, 1 << 30,
+                                 None) == hd.HD_ERR_ARG                                   # dst overlaps src
+    assert lib.hybrid_part_apply(ctypes.byref(ok), sums, 0x10010, 1 << 30, None) == hd.HD_ERR_WORKSPACE
+
+
 def test_header_is_plain_c_and_links(tmp_path):
     """The ABI header compiles as C99 (no C++ in its declarations) and a C
     program that takes the address of every entry point links against the
