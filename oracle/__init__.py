@@ -11,8 +11,9 @@ What each function follows in the paper:
 * ``amf``          - Algorithm 1, step 6 (adaptive median, level A / level B,
                      window growth k = 3..Smax over the noisy image).
 * ``wiener``       - Algorithm 1, step 4d, in the spatial local-statistics
-                     form (local mean / variance over w x w, noise variance =
-                     mean local variance unless supplied).
+                     form (local mean / variance over a wh x w window, square
+                     by default; noise variance = mean local variance unless
+                     supplied).
 * ``hybrid``       - Algorithm 1, step 4: Wiener(AMF(g)).  The contrast
                      stretch of step 4e is the separate ``contrast``.
 * ``amf_strips`` / ``hybrid_strips`` - Algorithm 1, step 6 as the listing
@@ -78,7 +79,9 @@ def _load():
             lib.oracle_amf.restype = I
             lib.oracle_wiener.argtypes = [P, L, L, I, I, ctypes.c_double, I, P, P, P, P, P, P]
             lib.oracle_wiener.restype = I
-            lib.oracle_wiener_stats.argtypes = [P, L, L, I, I, P, P]
+            lib.oracle_wiener_rect.argtypes = [P, L, L, I, I, I, ctypes.c_double, I, P, P, P, P, P, P]
+            lib.oracle_wiener_rect.restype = I
+            lib.oracle_wiener_stats.argtypes = [P, L, L, I, I, I, P, P]
             lib.oracle_wiener_stats.restype = I
             lib.oracle_amf_pixel.argtypes = [P, L, L, I, I, L, L]
             lib.oracle_amf_pixel.restype = I
@@ -155,8 +158,9 @@ class WienerResult:
 
 
 def wiener(f: np.ndarray, w: int, noise_var: float = -1.0, bits: int | None = None,
-           border_zero: bool = False) -> WienerResult:
-    """Local-statistics Wiener filter of the integer image ``f``.
+           border_zero: bool = False, wh: int | None = None) -> WienerResult:
+    """Local-statistics Wiener filter of the integer image ``f`` over a window
+    of ``wh`` rows (default ``w``: square) by ``w`` columns.
 
     ``noise_var < 0`` estimates the noise variance as the mean local variance.
     ``bits`` sets the output clamp 2^bits - 1 (default: 8 for uint8, 16 for uint16).
@@ -173,36 +177,39 @@ def wiener(f: np.ndarray, w: int, noise_var: float = -1.0, bits: int | None = No
     y32 = np.empty((H, W), dtype=np.float32)
     nu2 = ctypes.c_double()
     sumD = np.zeros(2, dtype=np.uint64)
-    rc = lib.oracle_wiener(_ptr(f16), H, W, int(w), int(bool(border_zero)), float(noise_var), maxv,
-                           _ptr(out64), _ptr(y64), _ptr(out32), _ptr(y32),
-                           ctypes.byref(nu2), _ptr(sumD))
+    rc = lib.oracle_wiener_rect(_ptr(f16), H, W, int(w if wh is None else wh), int(w), int(bool(border_zero)),
+                                float(noise_var), maxv, _ptr(out64), _ptr(y64), _ptr(out32), _ptr(y32),
+                                ctypes.byref(nu2), _ptr(sumD))
     if rc != ORACLE_OK:
         raise OracleError(rc, "oracle_wiener")
     total = int(sumD[0]) + (int(sumD[1]) << 64)
     return WienerResult(out64.astype(f.dtype), y64, out32.astype(f.dtype), y32, nu2.value, total)
 
 
-def wiener_stats(f: np.ndarray, w: int, border_zero: bool = False):
-    """(S1, D) per pixel as uint64 arrays, D = n*S2 - S1^2."""
+def wiener_stats(f: np.ndarray, w: int, border_zero: bool = False, wh: int | None = None):
+    """(S1, D) per pixel as uint64 arrays, D = n*S2 - S1^2, over ``wh`` rows
+    (default ``w``) by ``w`` columns, n = wh * w."""
     lib = _load()
     f16 = _as_u16(f)
     H, W = f16.shape
     S1 = np.empty((H, W), dtype=np.uint64)
     D = np.empty((H, W), dtype=np.uint64)
-    rc = lib.oracle_wiener_stats(_ptr(f16), H, W, int(w), int(bool(border_zero)), _ptr(S1), _ptr(D))
+    rc = lib.oracle_wiener_stats(_ptr(f16), H, W, int(w if wh is None else wh), int(w), int(bool(border_zero)),
+                                 _ptr(S1), _ptr(D))
     if rc != ORACLE_OK:
         raise OracleError(rc, "oracle_wiener_stats")
     return S1, D
 
 
 def hybrid(g: np.ndarray, smax: int, w: int, noise_var: float = -1.0, bits: int | None = None,
-           keep_unresolved: bool = False, border_zero: bool = False):
-    """Algorithm 1, step 4 without the contrast stretch: Wiener(AMF(g)).
+           keep_unresolved: bool = False, border_zero: bool = False, wh: int | None = None):
+    """Algorithm 1, step 4 without the contrast stretch: Wiener(AMF(g)), the
+    Wiener window ``wh`` rows (default ``w``) by ``w`` columns.
 
     Returns (f, WienerResult) where f is the adaptive-median output.
     """
     f = amf(g, smax, keep_unresolved=keep_unresolved)
-    return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero)
+    return f, wiener(f, w, noise_var=noise_var, bits=bits, border_zero=border_zero, wh=wh)
 
 
 def strip_bounds(H: int, parts: int) -> list[int]:

@@ -19,8 +19,9 @@
  * reading of the unresolved case) or keeps zxy (literal reading of the
  * listing, where the working copy starts as the input).
  *
- * Wiener (Algorithm 1, step 4d; spatial local-statistics form): over a w x w
- * window of the adaptive-median output f, n = w*w,
+ * Wiener (Algorithm 1, step 4d; spatial local-statistics form): over a
+ * wh x ww window of the adaptive-median output f (wh rows, ww columns, both
+ * odd; the paper gives no window, square ones are wh = ww = w), n = wh*ww,
  *   S1 = sum f, S2 = sum f^2 (exact integers), D = n*S2 - S1^2,
  *   mu = S1/n, sigma2 = D/n^2,
  *   nu2 = mean over all pixels of sigma2 (unless the caller supplies it)
@@ -140,19 +141,21 @@ int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
 }
 
 /*
- * Wiener local statistics: S1 and D = n*S2 - S1^2 for every pixel.
+ * Wiener local statistics over a wh x ww window (wh rows, ww columns, both
+ * odd; the square window is wh = ww = w): S1 and D = n*S2 - S1^2 for every
+ * pixel, n = wh*ww.
  * border_zero = 0: symmetric reflection; 1: zero outside, still counted in n.
  */
-static void wiener_stats(const uint16_t *f, long H, long W, int w, int border_zero,
+static void wiener_stats(const uint16_t *f, long H, long W, int wh, int ww, int border_zero,
                          uint64_t *S1_out, uint64_t *D_out)
 {
-    int r = w / 2;
-    uint64_t n = (uint64_t)w * (uint64_t)w;
+    int ry = wh / 2, rx = ww / 2;
+    uint64_t n = (uint64_t)wh * (uint64_t)ww;
     for (long y = 0; y < H; ++y) {
         for (long x = 0; x < W; ++x) {
             uint64_t S1 = 0, S2 = 0;
-            for (int dy = -r; dy <= r; ++dy) {
-                for (int dx = -r; dx <= r; ++dx) {
+            for (int dy = -ry; dy <= ry; ++dy) {
+                for (int dx = -rx; dx <= rx; ++dx) {
                     long yy = y + dy, xx = x + dx;
                     uint64_t v;
                     if (yy < 0 || yy >= H || xx < 0 || xx >= W) {
@@ -172,7 +175,7 @@ static void wiener_stats(const uint16_t *f, long H, long W, int w, int border_ze
 }
 
 /*
- * Wiener filter of an integer image f.
+ * Wiener filter of an integer image f over a wh x ww window.
  *   noise_var_in < 0 : estimate nu2 as the mean local variance of f
  *   maxv             : largest representable output value (2^bits - 1)
  * Outputs (each optional):
@@ -181,21 +184,21 @@ static void wiener_stats(const uint16_t *f, long H, long W, int w, int border_ze
  *   nu2_out     : the noise variance used
  *   sumD_out    : sum of D over all pixels as two 64-bit words {lo, hi}
  */
-int oracle_wiener(const uint16_t *f, long H, long W, int w, int border_zero,
-                  double noise_var_in, int maxv,
-                  uint16_t *out64, double *y64, uint16_t *out32, float *y32,
-                  double *nu2_out, uint64_t *sumD_out)
+int oracle_wiener_rect(const uint16_t *f, long H, long W, int wh, int ww, int border_zero,
+                       double noise_var_in, int maxv,
+                       uint16_t *out64, double *y64, uint16_t *out32, float *y32,
+                       double *nu2_out, uint64_t *sumD_out)
 {
     if (!f || H < 1 || W < 1 || maxv < 1) return ORACLE_ERR_ARG;
-    if (w < 1 || w % 2 == 0) return ORACLE_ERR_WINDOW;
+    if (wh < 1 || wh % 2 == 0 || ww < 1 || ww % 2 == 0) return ORACLE_ERR_WINDOW;
 
     long npx = H * W;
     uint64_t *S1 = (uint64_t *)malloc((size_t)npx * sizeof(uint64_t));
     uint64_t *D = (uint64_t *)malloc((size_t)npx * sizeof(uint64_t));
     if (!S1 || !D) { free(S1); free(D); return ORACLE_ERR_OOM; }
-    wiener_stats(f, H, W, w, border_zero, S1, D);
+    wiener_stats(f, H, W, wh, ww, border_zero, S1, D);
 
-    uint64_t n = (uint64_t)w * (uint64_t)w;
+    uint64_t n = (uint64_t)wh * (uint64_t)ww;
 
     /* global noise variance: exact integer sum, then binary64 */
     unsigned __int128 sumD = 0;
@@ -265,13 +268,24 @@ int oracle_wiener(const uint16_t *f, long H, long W, int w, int border_zero,
     return ORACLE_OK;
 }
 
-/* Per-pixel local statistics, exposed for the closed-form tests. */
-int oracle_wiener_stats(const uint16_t *f, long H, long W, int w, int border_zero,
+/* The square window w x w. */
+int oracle_wiener(const uint16_t *f, long H, long W, int w, int border_zero,
+                  double noise_var_in, int maxv,
+                  uint16_t *out64, double *y64, uint16_t *out32, float *y32,
+                  double *nu2_out, uint64_t *sumD_out)
+{
+    return oracle_wiener_rect(f, H, W, w, w, border_zero, noise_var_in, maxv, out64, y64, out32, y32,
+                              nu2_out, sumD_out);
+}
+
+/* Per-pixel local statistics over a wh x ww window, exposed for the
+ * closed-form tests. */
+int oracle_wiener_stats(const uint16_t *f, long H, long W, int wh, int ww, int border_zero,
                         uint64_t *S1_out, uint64_t *D_out)
 {
     if (!f || !S1_out || !D_out || H < 1 || W < 1) return ORACLE_ERR_ARG;
-    if (w < 1 || w % 2 == 0) return ORACLE_ERR_WINDOW;
-    wiener_stats(f, H, W, w, border_zero, S1_out, D_out);
+    if (wh < 1 || wh % 2 == 0 || ww < 1 || ww % 2 == 0) return ORACLE_ERR_WINDOW;
+    wiener_stats(f, H, W, wh, ww, border_zero, S1_out, D_out);
     return ORACLE_OK;
 }
 

@@ -37,38 +37,42 @@ def amf_brute(g, smax, keep_unresolved=False):
     return f, kk
 
 
-def window_values(f, y, x, w, border_zero=False):
-    """All w*w samples around (y, x) with the symmetric (or zero) border."""
+def window_values(f, y, x, w, border_zero=False, wh=None):
+    """All samples of the wh x w window (wh rows, default w) around (y, x)
+    with the symmetric (or zero) border."""
     f = np.asarray(f).astype(np.int64)
-    r = w // 2
+    wh = w if wh is None else wh
+    pad = ((wh // 2, wh // 2), (w // 2, w // 2))
     if border_zero:
-        ext = np.pad(f, r, mode="constant", constant_values=0)
+        ext = np.pad(f, pad, mode="constant", constant_values=0)
     else:
-        ext = np.pad(f, r, mode="symmetric")
-    return ext[y:y + w, x:x + w].ravel().tolist()
+        ext = np.pad(f, pad, mode="symmetric")
+    return ext[y:y + wh, x:x + w].ravel().tolist()
 
 
-def local_stats_exact(f, w, border_zero=False):
-    """Exact (mean, variance) per pixel as Fractions, two-pass formula."""
+def local_stats_exact(f, w, border_zero=False, wh=None):
+    """Exact (mean, variance) per pixel as Fractions, two-pass formula, over a
+    wh x w window (wh rows, default w)."""
     f = np.asarray(f)
     H, W = f.shape
-    n = w * w
+    n = w * (w if wh is None else wh)
     mu = [[None] * W for _ in range(H)]
     var = [[None] * W for _ in range(H)]
     for y in range(H):
         for x in range(W):
-            v = window_values(f, y, x, w, border_zero)
+            v = window_values(f, y, x, w, border_zero, wh)
             m = Fraction(sum(v), n)
             mu[y][x] = m
             var[y][x] = sum((Fraction(a) - m) ** 2 for a in v) / n
     return mu, var
 
 
-def wiener_exact(f, w, noise_var=None, border_zero=False):
-    """Exact rational Wiener output y and the exact noise variance."""
+def wiener_exact(f, w, noise_var=None, border_zero=False, wh=None):
+    """Exact rational Wiener output y and the exact noise variance (window wh
+    rows, default w, by w columns)."""
     f = np.asarray(f)
     H, W = f.shape
-    mu, var = local_stats_exact(f, w, border_zero)
+    mu, var = local_stats_exact(f, w, border_zero, wh)
     if noise_var is None:
         nu2 = sum(var[y][x] for y in range(H) for x in range(W)) / (H * W)
     else:

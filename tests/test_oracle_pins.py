@@ -282,6 +282,86 @@ def test_wiener_matches_scipy_with_zero_border():
         np.testing.assert_allclose(r.y64, ref, rtol=1e-9, atol=1e-9)
 
 
+# ---- rectangular windows: wh rows by ww columns
+RECT = [(1, 3), (3, 1), (3, 5), (5, 3), (1, 7), (7, 3), (5, 9)]
+
+
+@pytest.mark.parametrize("wh,ww", RECT)
+def test_wiener_rect_exact_rational(wh, ww):
+    rng = np.random.default_rng(wh * 100 + ww)
+    for H, W in [(1, 1), (2, 9), (7, 2), (6, 8)]:
+        f = rng.integers(0, 256, size=(H, W)).astype(np.uint8)
+        res = oracle.wiener(f, ww, wh=wh)
+        y_ex, nu2_ex, var = wiener_exact(f, ww, wh=wh)
+        n = wh * ww
+        assert res.sumD == sum(var[y][x] for y in range(H) for x in range(W)) * n * n
+        assert res.nu2 == pytest.approx(float(nu2_ex), rel=4e-16, abs=0)
+        y_ex2, _, _ = wiener_exact(f, ww, noise_var=Fraction(res.nu2), wh=wh)
+        for y in range(H):
+            for x in range(W):
+                assert abs(res.y64[y, x] - float(y_ex2[y, x])) <= 1e-9 * max(1.0, abs(float(y_ex2[y, x])))
+
+
+@pytest.mark.parametrize("wh,ww", RECT)
+def test_wiener_rect_checkerboard_closed_form(wh, ww):
+    # n = wh * ww is odd: interior windows hold one more cell of the colour of
+    # their corners (the centre's when ry + rx is even), so D = (n^2 - 1) d^2
+    # and S1 = n c +- d
+    c, d = 900, 23
+    H, W = 2 * wh + 5, 2 * ww + 6
+    yy, xx = np.mgrid[0:H, 0:W]
+    f = np.where((yy + xx) % 2 == 0, c + d, c - d).astype(np.uint16)
+    S1, D = oracle.wiener_stats(f, ww, wh=wh)
+    n = wh * ww
+    inner = (slice(wh // 2, H - wh // 2), slice(ww // 2, W - ww // 2))
+    np.testing.assert_array_equal(D[inner], np.full_like(D[inner], (n * n - 1) * d * d))
+    corner = -1 if (wh // 2 + ww // 2) % 2 else 1
+    sign = corner * np.where((yy + xx) % 2 == 0, 1, -1)[inner]
+    np.testing.assert_array_equal(S1[inner].astype(np.int64), n * c + sign * d)
+
+
+@pytest.mark.parametrize("wh,ww", [(3, 5), (5, 3), (1, 7), (7, 1)])
+def test_wiener_rect_ramps_fix_the_axes(wh, ww):
+    # a ramp along x varies only across the window's ww columns, a ramp along y
+    # only across its wh rows: variance a^2 r (r + 1) / 3 with r the radius of
+    # that axis (swapping the axes fails these)
+    a, b = 5, 40
+    H, W = 15, 17
+    n = wh * ww
+    fx = (a * np.arange(W)[None, :] + b + np.zeros((H, 1), np.int64)).astype(np.uint16)
+    S1, D = oracle.wiener_stats(fx, ww, wh=wh)
+    rx, ry = ww // 2, wh // 2
+    inner = (slice(ry, H - ry), slice(rx, W - rx))
+    assert np.all(D[inner] == n * n * a * a * rx * (rx + 1) // 3)
+    assert np.all(S1[inner] == n * fx[inner])
+    fy = (a * np.arange(H)[:, None] + b + np.zeros((1, W), np.int64)).astype(np.uint16)
+    S1, D = oracle.wiener_stats(fy, ww, wh=wh)
+    assert np.all(D[inner] == n * n * a * a * ry * (ry + 1) // 3)
+    assert np.all(S1[inner] == n * fy[inner])
+
+
+def test_wiener_rect_matches_scipy_with_zero_border():
+    from scipy.signal import wiener as scipy_wiener
+    rng = np.random.default_rng(19)
+    for wh, ww in [(3, 5), (5, 3), (1, 5), (7, 3)]:
+        f = rng.integers(0, 256, size=(29, 41)).astype(np.uint8)
+        r = oracle.wiener(f, ww, border_zero=True, wh=wh)
+        ref = scipy_wiener(f.astype(np.float64), mysize=(wh, ww))
+        np.testing.assert_allclose(r.y64, ref, rtol=1e-9, atol=1e-9)
+
+
+def test_wiener_rect_transpose_symmetry():
+    rng = np.random.default_rng(23)
+    f = rng.integers(0, 4096, size=(33, 21)).astype(np.uint16)
+    a = oracle.wiener(f, 7, bits=12, wh=3)
+    b = oracle.wiener(np.ascontiguousarray(f.T), 3, bits=12, wh=7)
+    np.testing.assert_array_equal(a.out64, b.out64.T)
+    np.testing.assert_array_equal(a.y64, b.y64.T)
+    assert a.sumD == b.sumD and a.nu2 == b.nu2
+    # wh = ww is the square window
+    np.testing.assert_array_equal(oracle.wiener(f, 5, bits=12, wh=5).y32, oracle.wiener(f, 5, bits=12).y32)
+
+
 @pytest.mark.parametrize("bits,w", [(8, 3), (8, 7), (12, 5), (12, 7), (16, 3), (16, 7)])
 def test_wiener_binary32_twin_error_bound(bits, w):
     rng = np.random.default_rng(bits * 10 + w)
