@@ -46,7 +46,7 @@ typedef enum {
     HD_OK = 0,
     HD_ERR_ARG = 1,        /* null pointer, bad size, bad pitch, overlap, bad enum */
     HD_ERR_SMAX = 2,       /* Smax not an odd integer in [3, HD_SMAX_MAX] (Alg. 1, step 6a) */
-    HD_ERR_WINDOW = 3,     /* Wiener window not odd in [1, HD_WIENER_W_MAX] */
+    HD_ERR_WINDOW = 3,     /* Wiener window side not odd in [1, HD_WIENER_W_MAX] */
     HD_ERR_DTYPE = 4,      /* unknown dtype or bits outside 1..16 (8 for HD_U8) */
     HD_ERR_WORKSPACE = 5,  /* workspace missing, misaligned or smaller than required */
     HD_ERR_CUDA = 6,       /* a CUDA runtime call failed */
@@ -81,6 +81,8 @@ typedef struct {
     int border;          /* hd_border, Wiener stage (the median always reflects) */
     int unresolved;      /* hd_unresolved */
     int bits;            /* significant bits: 8 for HD_U8; 1..16 for HD_U16 */
+    int wiener_h;        /* Wiener window rows, odd, 1..HD_WIENER_W_MAX; 0 = wiener_w
+                            (square window).  The paper gives no window size. */
 } hd_params;
 
 /* One image and where its result goes. */
@@ -107,7 +109,8 @@ typedef struct {
 hd_status amf_filter(const hd_image *img, hd_stream_t stream);
 
 /* Wiener filter of an already median-filtered image (Algorithm 1, step 4d;
- * local-statistics form).  Over the w x w window, n = w*w, with exact integer
+ * local-statistics form).  Over the window of h = wiener_h rows (wiener_w when
+ * 0) by w = wiener_w columns, n = h*w, with exact integer
  * S1 = sum f, S2 = sum f^2 and D = n*S2 - S1^2:
  *   mu = S1/n, sigma2 = D/n^2,
  *   nu2 = noise_var if >= 0, else fl(fl(sum of D over all pixels) / (n^2 H W)),
@@ -247,7 +250,7 @@ hd_status hybrid_denoise_static(const hd_image *img, hd_stream_t stream);
  *   H, W:     the WHOLE image.
  *   buf_row0, buf_rows: the rows src holds, [buf_row0, buf_row0 + buf_rows).
  *             They must include [max(0, own_row0 - h), min(H, own_row0 +
- *             own_rows + h)), h = hd_part_halo_rows() = smax/2 + wiener_w/2.
+ *             own_rows + h)), h = hd_part_halo_rows() = smax/2 + (window rows)/2.
  *   own_row0, own_rows: the rows this part owns and writes.
  *   src:      device, buf_rows rows of src_pitch bytes (the noisy image).
  *   dst:      device, own_rows rows of dst_pitch bytes: dst row 0 is image

@@ -48,7 +48,8 @@ EXPORTS = [
 
 class hd_params(ctypes.Structure):
     _fields_ = [("smax", ctypes.c_int), ("wiener_w", ctypes.c_int), ("noise_var", ctypes.c_double),
-                ("border", ctypes.c_int), ("unresolved", ctypes.c_int), ("bits", ctypes.c_int)]
+                ("border", ctypes.c_int), ("unresolved", ctypes.c_int), ("bits", ctypes.c_int),
+                ("wiener_h", ctypes.c_int)]
 
 
 class hd_image(ctypes.Structure):
@@ -162,11 +163,12 @@ class Params:
     border: int = HD_BORDER_SYMMETRIC
     unresolved: int = HD_UNRESOLVED_ZMED
     bits: int | None = None
+    wiener_h: int = 0          # Wiener window rows; 0: square (wiener_w)
 
     def to_c(self, dtype_code: int) -> hd_params:
         bits = self.bits if self.bits is not None else (8 if dtype_code == HD_U8 else 16)
         return hd_params(int(self.smax), int(self.wiener_w), float(self.noise_var), int(self.border),
-                         int(self.unresolved), int(bits))
+                         int(self.unresolved), int(bits), int(self.wiener_h))
 
 
 def _torch():
@@ -273,9 +275,11 @@ def hybrid_host_workspace_size(H: int, W: int, dtype_code: int, params: Params) 
 
 
 def wiener_filter(src, dst, wiener_w: int = 5, noise_var: float = -1.0, border: int = HD_BORDER_SYMMETRIC,
-                  bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None):
-    """Local-statistics Wiener filter (Algorithm 1, step 4d) of ``src`` into ``dst``."""
-    p = Params(wiener_w=wiener_w, noise_var=noise_var, border=border, bits=bits)
+                  bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None,
+                  wiener_h: int = 0):
+    """Local-statistics Wiener filter (Algorithm 1, step 4d) of ``src`` into
+    ``dst`` over a window of ``wiener_h`` rows (0: square) by ``wiener_w`` columns."""
+    p = Params(wiener_w=wiener_w, noise_var=noise_var, border=border, bits=bits, wiener_h=wiener_h)
     img = make_image(src, dst, p, noise_var_out, y_out)
     if workspace is None:
         workspace = _workspace(wiener_workspace_size(img.H, img.W, img.dtype, p), src.device)
@@ -350,9 +354,11 @@ def contrast_stretch(src, dst=None, tol: float = 0.01, bits: int | None = None, 
 
 def hybrid_denoise(src, dst, smax: int = 11, wiener_w: int = 5, noise_var: float = -1.0,
                    border: int = HD_BORDER_SYMMETRIC, unresolved: int = HD_UNRESOLVED_ZMED,
-                   bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None):
-    """Hybrid denoise: Wiener(AdaptiveMedian(src)) into ``dst`` (Algorithm 1, step 4)."""
-    p = Params(smax, wiener_w, noise_var, border, unresolved, bits)
+                   bits: int | None = None, workspace=None, noise_var_out=None, y_out=None, stream=None,
+                   wiener_h: int = 0):
+    """Hybrid denoise: Wiener(AdaptiveMedian(src)) into ``dst`` (Algorithm 1,
+    step 4); the Wiener window is ``wiener_h`` rows (0: square) by ``wiener_w``."""
+    p = Params(smax, wiener_w, noise_var, border, unresolved, bits, wiener_h)
     img = make_image(src, dst, p, noise_var_out, y_out)
     if workspace is None:
         workspace = _workspace(hybrid_workspace_size(img.H, img.W, img.dtype, p), src.device)

@@ -48,6 +48,9 @@ hd_tuning current_tuning()
 
 int elem_size(int dtype) { return dtype == HD_U8 ? 1 : 2; }
 
+// Rows of the Wiener window: wiener_h, or wiener_w when it is 0 (square).
+int window_rows(const hd_params &p) { return p.wiener_h ? p.wiener_h : p.wiener_w; }
+
 // Checks shared by every entry point.  `need_amf` / `need_wiener` select the
 // parameter checks of the stages the call runs.
 hd_status check_image(const hd_image *img, bool need_amf, bool need_wiener, bool host_buffers)
@@ -77,8 +80,9 @@ hd_status check_image(const hd_image *img, bool need_amf, bool need_wiener, bool
             return HD_ERR_ARG;
     }
     if (need_wiener) {
-        const int w = img->p.wiener_w;
+        const int w = img->p.wiener_w, wh = window_rows(img->p);
         if (w < 1 || w > HD_WIENER_W_MAX || (w & 1) == 0) return HD_ERR_WINDOW;
+        if (wh < 1 || wh > HD_WIENER_W_MAX || (wh & 1) == 0) return HD_ERR_WINDOW;
         if (img->p.border != HD_BORDER_SYMMETRIC && img->p.border != HD_BORDER_ZERO) return HD_ERR_ARG;
         if (!(img->p.noise_var == img->p.noise_var)) return HD_ERR_ARG;   // NaN
         if (img->y_out && ((uintptr_t)img->y_out & 3)) return HD_ERR_ARG;
@@ -136,7 +140,7 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     d.noise_var = img->p.noise_var;
     {
         // the host's IEEE division gives the correctly rounded reciprocal
-        const double nw = (double)img->p.wiener_w * (double)img->p.wiener_w;
+        const double nw = (double)img->p.wiener_w * (double)window_rows(img->p);
         d.inv_den = 1.0 / (nw * nw * (double)img->H * (double)img->W);
     }
     d.noise_var_out = img->noise_var_out;
@@ -148,13 +152,15 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
     d.maxv = (int)((1u << img->p.bits) - 1u);
     d.smax = img->p.smax;
     d.w = img->p.wiener_w;
+    d.wh = window_rows(img->p);
     d.unresolved = img->p.unresolved;
     d.border_zero = img->p.border == HD_BORDER_ZERO;
     d.mode = mode;
     // same tile shape as the kernel: left margin rw rounded up to even, width even
     const int rw = mode == MODE_AMF ? 0 : img->p.wiener_w / 2;
+    const int ry = mode == MODE_AMF ? 0 : window_rows(img->p) / 2;
     const int lm = rw + (rw & 1);
-    const int TW = (64 - lm - rw) & ~1, TH = t.region_h - 2 * rw;
+    const int TW = (64 - lm - rw) & ~1, TH = t.region_h - 2 * ry;
     d.tiles_x = (img->W + TW - 1) / TW;
     d.tiles_y = (img->H + TH - 1) / TH;
     d.p2_items = plane ? 0 : d.tiles_x * d.tiles_y;
@@ -169,8 +175,8 @@ ImgDesc make_desc(const hd_image *img, int mode, const hd_tuning &t, ImgCtl *ctl
 bool image_wide(const ImgDesc &d)
 {
     if (d.mode == MODE_AMF) return false;
-    const long long n = (long long)d.w * d.w;
-    return !(d.maxv < 0x8000 && (long long)(d.w + 1) * d.maxv <= 65535 && n * d.maxv < 131072);
+    const long long n = (long long)d.w * d.wh;
+    return !(d.maxv < 0x8000 && (long long)(std::max(d.w, d.wh) + 1) * d.maxv <= 65535 && n * d.maxv < 131072);
 }
 
 int halo_a(const ImgDesc &d) { return (d.mode == MODE_AMF || d.mode == MODE_HYBRID_EST || d.mode == MODE_HYBRID_GIVEN) ? d.smax / 2 : 0; }
@@ -1122,16 +1128,17 @@ static hd_status check_part(const hd_part *pt, bool need_dst)
     if (pt->dtype == HD_U16 && (pt->p.bits < 1 || pt->p.bits > 16)) return HD_ERR_DTYPE;
     if (pt->H < 1 || pt->W < 1) return HD_ERR_ARG;
     if (pt->H > HD_DIM_MAX || pt->W > HD_DIM_MAX) return HD_ERR_OVERFLOW;
-    const int s = pt->p.smax, w = pt->p.wiener_w;
+    const int s = pt->p.smax, w = pt->p.wiener_w, wh = window_rows(pt->p);
     if (s < 3 || s > HD_SMAX_MAX || (s & 1) == 0) return HD_ERR_SMAX;
     if (w < 1 || w > HD_WIENER_W_MAX || (w & 1) == 0) return HD_ERR_WINDOW;
+    if (wh < 1 || wh > HD_WIENER_W_MAX || (wh & 1) == 0) return HD_ERR_WINDOW;
     if (pt->p.unresolved != HD_UNRESOLVED_ZMED && pt->p.unresolved != HD_UNRESOLVED_KEEP) return HD_ERR_ARG;
     if (pt->p.border != HD_BORDER_SYMMETRIC && pt->p.border != HD_BORDER_ZERO) return HD_ERR_ARG;
     // only the estimated noise variance needs the exchange of sums
     if (!(pt->p.noise_var < 0.0)) return HD_ERR_ARG;
     // rows: the part's own rows inside its buffer, the buffer inside the image,
     // and the buffer holding every halo row the own rows' windows read
-    const int h = s / 2 + w / 2;
+    const int h = s / 2 + wh / 2;
     if (pt->buf_row0 < 0 || pt->buf_rows < 1 || pt->buf_row0 + pt->buf_rows > pt->H) return HD_ERR_ARG;
     if (pt->own_rows < 1 || pt->own_row0 < pt->buf_row0 ||
         pt->own_row0 + pt->own_rows > pt->buf_row0 + pt->buf_rows)
@@ -1182,11 +1189,11 @@ static ImgDesc part_desc(const hd_part *pt, const hd_tuning &t, uint8_t *ws)
     // output row y of the buffer goes to row y - own0 of the part's own rows
     d.dst = static_cast<uint8_t *>(pt->dst) - (ptrdiff_t)own0 * (ptrdiff_t)pt->dst_pitch;
     {
-        const double nw = (double)pt->p.wiener_w * (double)pt->p.wiener_w;
+        const double nw = (double)pt->p.wiener_w * (double)window_rows(pt->p);
         d.inv_den = 1.0 / (nw * nw * (double)pt->H * (double)pt->W);
     }
-    const int rw = pt->p.wiener_w / 2;
-    const int TH = t.region_h - 2 * rw;
+    const int ry = window_rows(pt->p) / 2;
+    const int TH = t.region_h - 2 * ry;
     d.tiles_y = (pt->own_rows + TH - 1) / TH;
     d.p2_items = 0;
     return d;
@@ -1235,8 +1242,10 @@ hd_status hd_part_halo_rows(const hd_params *p, int *rows)
 {
     if (!p || !rows) return HD_ERR_ARG;
     if (p->smax < 3 || p->smax > HD_SMAX_MAX || (p->smax & 1) == 0) return HD_ERR_SMAX;
+    const int wh = window_rows(*p);
     if (p->wiener_w < 1 || p->wiener_w > HD_WIENER_W_MAX || (p->wiener_w & 1) == 0) return HD_ERR_WINDOW;
-    *rows = p->smax / 2 + p->wiener_w / 2;
+    if (wh < 1 || wh > HD_WIENER_W_MAX || (wh & 1) == 0) return HD_ERR_WINDOW;
+    *rows = p->smax / 2 + wh / 2;
     return HD_OK;
 }
 

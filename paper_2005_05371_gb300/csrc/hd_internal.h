@@ -1,8 +1,9 @@
 // hd_internal.h -- types shared by the persistent kernel and the host API.
 //
-// Work decomposition: every image is cut into output tiles of
-// (64 - 2 Rw) x (region_h - 2 Rw) pixels, Rw = w/2 (0 for the median alone), so
-// that tile plus Wiener halo is a 64 x region_h region.  A work item is
+// Work decomposition: every image is cut into output tiles of about
+// (64 - 2 Rw) x (region_h - 2 Ry) pixels, Rw = w/2 and Ry = wh/2 the Wiener
+// window's column and row radii (0 for the median alone), so that tile plus
+// Wiener halo is a 64 x region_h region.  A work item is
 // (image, phase, tile).  Items are taken in ticket
 // order from one global counter by the CTAs of a persistent grid, so a CTA
 // only ever waits on items that running CTAs already hold.
@@ -53,7 +54,8 @@ struct ImgDesc {
     int elem;                 // bytes per pixel: 1 or 2
     int maxv;                 // 2^bits - 1
     int smax;                 // odd >= 3 (ignored when the mode has no median)
-    int w;                    // odd >= 1 (ignored when the mode has no Wiener stage)
+    int w;                    // Wiener window columns, odd >= 1 (ignored when the mode has no Wiener stage)
+    int wh;                   // Wiener window rows, odd >= 1
     int unresolved;           // 0: zmed of Smax window, 1: keep input
     int border_zero;          // Wiener border: 0 symmetric, 1 zero
     int mode;

@@ -140,10 +140,10 @@ __host__ __device__ inline SmemLayout layout(int FH, int ra_max, int wide)
 struct Geo {
     int x0, y0;      // output tile origin (image coordinates)
     int tw, th;      // output tile size (clipped at the image edge)
-    int Rw, Lm, hx;  // Wiener halo (rows above/below, columns right), left margin, Lm - Rw
+    int Rw, Ry, Lm, hx;  // Wiener halo (columns right: Rw, rows above/below: Ry), left margin, Lm - Rw
     int Ra, pa;      // median halo, column pad of the g region (Ra + pa is even)
     int GS;          // g-region row stride (u16)
-    int ncol, nrow;  // f-region size: Lm + tw + Rw columns, th + 2 Rw rows
+    int ncol, nrow;  // f-region size: Lm + tw + Rw columns, th + 2 Ry rows
     int gfx, gfy;    // image coordinates of f-region cell (0, 0)
 };
 
@@ -1147,16 +1147,16 @@ struct ApplyConst {
 template <bool NARROW, bool PLANE>
 __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, void *h2p, BlockShared &bs)
 {
-    const int w = d.w;
+    const int w = d.w, wy = d.wh;      // window columns, rows
     constexpr bool with_plane = PLANE;
     hsums<NARROW>(g, fs, H1, h2p, w, with_plane);
     const bool zero = d.border_zero != 0;
     const int gy0 = g.y0 + d.gy_off;       // the tile's first row in the whole image
-    const bool interior = !zero && gy0 >= g.Rw && gy0 + g.th <= d.Hg - g.Rw && g.x0 >= g.Rw &&
+    const bool interior = !zero && gy0 >= g.Ry && gy0 + g.th <= d.Hg - g.Ry && g.x0 >= g.Rw &&
                           g.x0 + g.tw <= d.W - g.Rw;
     if (!interior) {
         for (int i = threadIdx.x; i < g.th + g.tw; i += kThreads) {
-            if (i < g.th) bs.my[i] = window_multiplicity(gy0 + i, d.Hg, g.Rw, zero);
+            if (i < g.th) bs.my[i] = window_multiplicity(gy0 + i, d.Hg, g.Ry, zero);
             else bs.mx[i - g.th] = window_multiplicity(g.x0 + i - g.th, d.W, g.Rw, zero);
         }
     }
@@ -1168,13 +1168,13 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     u64 accA = 0, accB = 0;
     if (x < g.tw && j0 < j1) {
         const bool two = x + 1 < g.tw;
-        const u32 n = (u32)(w * w);
+        const u32 n = (u32)(w * wy);
         const float inv_n = __frcp_rn((float)n), inv_n2 = __frcp_rn((float)(n * n));
         const u32 *H2n = reinterpret_cast<const u32 *>(h2p);
         const u64 *H2w = reinterpret_cast<const u64 *>(h2p);
         u32 sa = 0, sb = 0, qa = 0, qb = 0;
         u64 wa = 0, wb = 0;
-        for (int t = 0; t < w; ++t) {
+        for (int t = 0; t < wy; ++t) {
             const uint2 h = *reinterpret_cast<const uint2 *>(H1 + (j0 + t) * HS + x);
             sa += h.x;
             sb += h.y;
@@ -1194,7 +1194,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         const bool pair16 = two && ((d.W | g.x0) & 1) == 0 &&
                             (reinterpret_cast<uintptr_t>(d.plane) & 15) == 0;   // (mu, s2) pairs land 16-byte aligned
         for (int j = j0; j < j1; ++j) {
-            const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
+            const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Ry) * FS + g.Lm + x);
             const u32 fa = fp & 0xffffu, fb = fp >> 16;
             if (interior) {
                 accA += (u64)sa * sa + (two ? (u64)sb * sb : 0ull);
@@ -1228,27 +1228,27 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
                 pp += d.W;
             }
             if (j + 1 < j1) {
-                const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
+                const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + wy) * HS + x);
                 const uint2 ho_ = *reinterpret_cast<const uint2 *>(H1 + j * HS + x);
                 sa += hi_.x - ho_.x;
                 sb += hi_.y - ho_.y;
                 if (with_plane) {
                     if (NARROW) {
-                        const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + w) * HS + x);
+                        const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + wy) * HS + x);
                         const uint2 qo = *reinterpret_cast<const uint2 *>(H2n + j * HS + x);
                         qa += qi.x - qo.x;
                         qb += qi.y - qo.y;
                     } else {
-                        wa += H2w[(j + w) * HS + x];
+                        wa += H2w[(j + wy) * HS + x];
                         wa -= H2w[j * HS + x];
-                        wb += H2w[(j + w) * HS + x + 1];
+                        wb += H2w[(j + wy) * HS + x + 1];
                         wb -= H2w[j * HS + x + 1];
                     }
                 }
             }
         }
     }
-    if (interior) accB *= (u64)w * (u64)w;
+    if (interior) accB *= (u64)w * (u64)wy;
     accA = warp_sum_u64(accA);
     accB = warp_sum_u64(accB);
     if (lane == 0) {
@@ -1499,11 +1499,11 @@ __device__ void p2_apply(const ImgDesc &d, const unsigned char *sb, const P2Stag
 template <bool NARROW>
 __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, void *h2p, float v2f)
 {
-    const int w = d.w;
+    const int w = d.w, wy = d.wh;      // window columns, rows
     hsums<NARROW>(g, fs, H1, h2p, w, true);
     __syncthreads();
     ApplyConst k;
-    k.n = (u32)(w * w);
+    k.n = (u32)(w * wy);
     k.v2f = v2f;
     k.inv_n = __frcp_rn((float)k.n);
     k.inv_n2 = __frcp_rn((float)(k.n * k.n));
@@ -1519,7 +1519,7 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     u32 sa = 0, sb = 0;
     u32 qa = 0, qb = 0;       // NARROW: S2 mod 2^32
     u64 wa = 0, wb = 0;       // WIDE
-    for (int t = 0; t < w; ++t) {
+    for (int t = 0; t < wy; ++t) {
         const uint2 h = *reinterpret_cast<const uint2 *>(H1 + (j0 + t) * HS + x);
         sa += h.x;
         sb += h.y;
@@ -1541,7 +1541,7 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
             da = __ull2float_rn((u64)k.n * wa - (u64)sa * sa);
             db = __ull2float_rn((u64)k.n * wb - (u64)sb * sb);
         }
-        const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Rw) * FS + g.Lm + x);
+        const u32 fp = *reinterpret_cast<const u32 *>(fs + (j + g.Ry) * FS + g.Lm + x);
         float ya, yb;
         const u32 oa = wiener_px(sa, da, fp & 0xffffu, k, ya);
         const u32 ob = wiener_px(sb, db, fp >> 16, k, yb);
@@ -1567,19 +1567,19 @@ __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
             if (two) yp[1] = yb;
         }
         if (j + 1 < j1) {
-            const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + w) * HS + x);
+            const uint2 hi_ = *reinterpret_cast<const uint2 *>(H1 + (j + wy) * HS + x);
             const uint2 ho_ = *reinterpret_cast<const uint2 *>(H1 + j * HS + x);
             sa += hi_.x - ho_.x;
             sb += hi_.y - ho_.y;
             if (NARROW) {
-                const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + w) * HS + x);
+                const uint2 qi = *reinterpret_cast<const uint2 *>(H2n + (j + wy) * HS + x);
                 const uint2 qo = *reinterpret_cast<const uint2 *>(H2n + j * HS + x);
                 qa += qi.x - qo.x;
                 qb += qi.y - qo.y;
             } else {
-                wa += H2w[(j + w) * HS + x];
+                wa += H2w[(j + wy) * HS + x];
                 wa -= H2w[j * HS + x];
-                wb += H2w[(j + w) * HS + x + 1];
+                wb += H2w[(j + wy) * HS + x + 1];
                 wb -= H2w[j * HS + x + 1];
             }
         }
@@ -1613,11 +1613,11 @@ __device__ __forceinline__ bool mode_median(int mode)
 }
 
 // Tile geometry of an image with Wiener halo rw (0 for the median alone).
-__device__ __forceinline__ void tile_shape(int rw, int FH, int &Lm, int &TW, int &TH)
+__device__ __forceinline__ void tile_shape(int rw, int ry, int FH, int &Lm, int &TW, int &TH)
 {
     Lm = rw + (rw & 1);
     TW = (FW - Lm - rw) & ~1;
-    TH = FH - 2 * rw;
+    TH = FH - 2 * ry;
 }
 
 template <bool PACK, bool NARROW>
@@ -1646,7 +1646,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         if (d.smax > 3)
             amf_grow<PACK>(d, g, vw.gs, vw.fs, vw.wl0, vw.wl1, bs.cnt, FH * FW, vw.st_mm, vw.st_c,
                            lp.small_growth, lp.select_lanes);
-        if (g.Rw > 0 && d.border_zero) {
+        if ((g.Rw > 0 || g.Ry > 0) && d.border_zero) {
             // zero-border Wiener: samples outside the image read 0 (after every
             // growth write: the short-worklist path ends without a barrier)
             __syncthreads();
@@ -1675,7 +1675,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         return;
     }
     if (phase == 1 && mode == MODE_HYBRID_EST) {
-        store_region(vw.fs + g.Rw * FS + g.Lm, FS, g.th, g.tw, d.fbuf, d.f_pitch, d.elem, g.y0, g.x0);
+        store_region(vw.fs + g.Ry * FS + g.Lm, FS, g.th, g.tw, d.fbuf, d.f_pitch, d.elem, g.y0, g.x0);
         HD_STAMP(3);
     }
     if (phase == 1 && est) {
@@ -1688,7 +1688,7 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     // value is cached per CTA for the image's following tiles
     if (threadIdx.x == 0) {
         if (!est || bs.nu2_of != d.ctl) {
-            const u64 n = (u64)d.w * (u64)d.w;
+            const u64 n = (u64)d.w * (u64)d.wh;
             const double nu2 = est ? noise_variance(d.ctl, n, d.Hg, d.W, d.inv_den) : d.noise_var;
             bs.nu2 = nu2;
             bs.nu2f = __double2float_rn(nu2);
@@ -1738,7 +1738,7 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
         }
     }
     if (threadIdx.x == 32) {
-        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.w, d.Hg, d.W, d.inv_den);
+        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.wh, d.Hg, d.W, d.inv_den);
         bs.nu2 = nu2;
         bs.nu2f = __double2float_rn(nu2);
         if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
@@ -1780,8 +1780,8 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
 
 __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
 {
-    const long long n = (long long)d.w * d.w;
-    return d.maxv < 0x8000 && (long long)(d.w + 1) * d.maxv <= 65535 && n * d.maxv < 131072;
+    const long long n = (long long)d.w * d.wh;
+    return d.maxv < 0x8000 && (long long)(max(d.w, d.wh) + 1) * d.maxv <= 65535 && n * d.maxv < 131072;
 }
 
 __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchParams &lp, const Views &vw,
@@ -1789,8 +1789,9 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
 {
     Geo g;
     g.Rw = d.mode == MODE_AMF ? 0 : (d.w >> 1);
+    g.Ry = d.mode == MODE_AMF ? 0 : (d.wh >> 1);
     int TW, TH;
-    tile_shape(g.Rw, lp.region_h, g.Lm, TW, TH);
+    tile_shape(g.Rw, g.Ry, lp.region_h, g.Lm, TW, TH);
     g.hx = g.Lm - g.Rw;
     g.Ra = (phase == 1 && mode_median(d.mode)) ? (d.smax >> 1) : 0;
     g.pa = g.Ra & 1;
@@ -1801,9 +1802,9 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
     g.tw = min(TW, d.W - g.x0);
     g.th = min(TH, d.own1 - g.y0);
     g.ncol = g.Lm + g.tw + g.Rw;
-    g.nrow = g.th + 2 * g.Rw;
+    g.nrow = g.th + 2 * g.Ry;
     g.gfx = g.x0 - g.Lm;
-    g.gfy = g.y0 - g.Rw;
+    g.gfy = g.y0 - g.Ry;
 
     if (phase == 2 && bs.nu2_of != d.ctl) {
         HD_STAMP_INIT();

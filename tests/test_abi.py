@@ -68,6 +68,18 @@ def test_window_rejected(w):
     assert call("hybrid_denoise", _img(w=w)) == hd.HD_ERR_WINDOW
 
 
+@pytest.mark.parametrize("wh", [-1, 2, 4, 17])
+def test_window_rows_rejected(wh):
+    img = _img(w=5)
+    img.p.wiener_h = wh
+    assert call("wiener_filter", img) == hd.HD_ERR_WINDOW
+    assert call("hybrid_denoise", img) == hd.HD_ERR_WINDOW
+    assert call("amf_filter", img) != hd.HD_ERR_WINDOW           # the median ignores the Wiener window
+    p = hd.Params(7, 5, wiener_h=wh).to_c(hd.HD_U8)
+    n = ctypes.c_int()
+    assert hd._lib.hd_part_halo_rows(ctypes.byref(p), ctypes.byref(n)) == hd.HD_ERR_WINDOW
+
+
 def test_bad_arguments_rejected():
     assert call("amf_filter", _img(src=0)) == hd.HD_ERR_ARG
     assert call("amf_filter", _img(dst=0)) == hd.HD_ERR_ARG
