@@ -24,6 +24,10 @@ What each function follows in the paper:
                      runs on the whole reassembled image.
 * ``reference_noise_variance`` - Algorithm 1, step 4d with the original
                      image passed to the Wiener stage: nu2 = mean (f - ref)^2.
+* ``wiener_deconv`` - the Wiener filter as Section IV places it, in the
+                     Fourier domain: deconvolution by a point-spread function
+                     with a noise-to-signal ratio (both the caller's; the
+                     paper gives neither), circular boundary, binary64.
 * ``contrast``     - Algorithm 1, step 4e (the paper gives no rule): linear
                      stretch between the k-th smallest and k-th largest
                      values, k = floor(tol * N), exact integer rounding.
@@ -272,3 +276,36 @@ def reference_noise_variance(f: np.ndarray, ref: np.ndarray):
     if rc != ORACLE_OK:
         raise OracleError(rc, "oracle_reference_noise_var")
     return nu2.value, int(tot[0])
+
+
+def psf_transfer(psf: np.ndarray, H: int, W: int) -> np.ndarray:
+    """The PSF's transfer function on the H x W frequency grid: the PSF placed
+    on an H x W grid with its centre tap (row kh // 2, column kw // 2) at the
+    origin and the other taps wrapped around, then its 2-D DFT (binary64)."""
+    psf = np.asarray(psf, dtype=np.float64)
+    kh, kw = psf.shape
+    P = np.zeros((H, W), dtype=np.float64)
+    for i in range(kh):
+        for j in range(kw):
+            P[(i - kh // 2) % H, (j - kw // 2) % W] += psf[i, j]
+    return np.fft.fft2(P)
+
+
+def wiener_deconv(g: np.ndarray, psf: np.ndarray, nsr: float, bits: int | None = None):
+    """Frequency-domain Wiener filter (Section IV): with G the 2-D DFT of the
+    image and P the PSF's transfer function, the estimate's spectrum is
+    F = conj(P) / (|P|^2 + nsr) * G, and the estimate y the real part of the
+    inverse DFT of F (the DFT's periodic extension is the border rule).
+    out = min(maxv, max(0, floor(y + 1/2))).  Returns (out, y) with y in
+    binary64."""
+    g = np.asarray(g)
+    if bits is None:
+        bits = 8 if g.dtype == np.uint8 else 16
+    maxv = (1 << int(bits)) - 1
+    H, W = g.shape
+    P = psf_transfer(psf, H, W)
+    G = np.fft.fft2(g.astype(np.float64))
+    F = np.conj(P) / (np.abs(P) ** 2 + float(nsr)) * G
+    y = np.real(np.fft.ifft2(F))
+    out = np.clip(np.floor(y + 0.5), 0, maxv).astype(g.dtype)
+    return out, y
