@@ -305,6 +305,33 @@ hd_status reference_noise_variance(const void *f, size_t f_pitch, const void *re
                                    int W, int dtype, double *nu2_out, void *workspace, size_t ws_bytes,
                                    hd_stream_t stream);
 
+/* ---------------------------------------------------------------- Fourier domain
+ * The Wiener filter in the Fourier domain, where Section IV places the
+ * hybrid's Wiener stage: deconvolution by a point-spread function with a
+ * noise-to-signal ratio (the paper gives neither; both are the caller's).
+ * With G the 2-D DFT of src and P the PSF's transfer function (the PSF placed
+ * on the H x W grid with its centre tap, row kh/2 and column kw/2, at the
+ * origin and the other taps wrapped around),
+ *   F = conj(P) / (|P|^2 + nsr) * G,   y = Re IDFT(F),
+ *   dst = min(2^bits - 1, max(0, floor(y + 1/2))),
+ * with the DFT's periodic extension as the border rule (circular boundary).
+ * Arithmetic: binary32 transforms (radix 2, and Bluestein's method for other
+ * lengths) with twiddles rounded from binary64; tests bound |y - y64|.
+ *   img: src, dst device images (H x W, same dtype; no overlap), p.bits;
+ *        y_out optional (binary32 y, pitch W floats); the other fields are
+ *        ignored.  H and W: powers of two up to 8192, or any length up to
+ *        4096; else HD_ERR_OVERFLOW.
+ *   psf: device, kh x kw binary32, row-major, 1 <= kh, kw <= HD_PSF_MAX.
+ *   nsr: >= 0 and finite (nsr = 0 with a PSF whose transfer function
+ *        vanishes somewhere divides by zero, as the formula does).
+ *   workspace: device, 256-byte aligned, >= wiener_deconv_workspace_size()
+ *        (three H x W complex planes and the transform tables).
+ * Ten kernel launches, no device-side waits. */
+#define HD_PSF_MAX 255
+hd_status wiener_deconv_workspace_size(int H, int W, size_t *bytes);
+hd_status wiener_deconvolve(const hd_image *img, const float *psf, int kh, int kw, double nsr, void *workspace,
+                            size_t ws_bytes, hd_stream_t stream);
+
 /* ---------------------------------------------------------------- contrast
  * Contrast stretch, the post-processing step of the hybrid (Algorithm 1,
  * step 4e).  The paper gives no rule; this is a linear stretch between two

@@ -43,6 +43,7 @@ EXPORTS = [
     "hd_batch_pipeline_workspace_size", "hd_batch_pipeline_create", "hd_batch_pipeline_submit",
     "hd_batch_pipeline_wait", "hd_batch_pipeline_destroy",
     "hd_part_halo_rows", "hybrid_part_workspace_size", "hybrid_part_stats", "hybrid_part_apply",
+    "wiener_deconv_workspace_size", "wiener_deconvolve",
 ]
 
 
@@ -122,6 +123,8 @@ def _load() -> ctypes.CDLL:
         "hd_batch_pipeline_wait": ([P], I),
         "hd_batch_pipeline_destroy": ([P], I),
         "hd_part_halo_rows": ([par_p, ctypes.POINTER(I)], I),
+        "wiener_deconv_workspace_size": ([I, I, ctypes.POINTER(S)], I),
+        "wiener_deconvolve": ([img_p, P, I, I, ctypes.c_double, P, S, P], I),
         "hybrid_part_workspace_size": ([ctypes.POINTER(hd_part), ctypes.POINTER(S)], I),
         "hybrid_part_stats": ([ctypes.POINTER(hd_part), P, S, P, P], I),
         "hybrid_part_apply": ([ctypes.POINTER(hd_part), P, P, S, P], I),
@@ -573,6 +576,33 @@ class BatchPipeline:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- Fourier domain
+HD_PSF_MAX = 255
+
+
+def wiener_deconv_workspace_size(H: int, W: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.wiener_deconv_workspace_size(int(H), int(W), ctypes.byref(n)), "wiener_deconv_workspace_size")
+    return n.value
+
+
+def wiener_deconvolve(src, dst, psf, nsr: float, bits: int | None = None, workspace=None, y_out=None,
+                      stream=None):
+    """The Wiener filter in the Fourier domain (Section IV): deconvolution of
+    ``src`` by the PSF (a float32 CUDA tensor, kh x kw) with noise-to-signal
+    ratio ``nsr``, into ``dst`` (circular boundary)."""
+    torch = _torch()
+    if psf.dtype != torch.float32 or psf.dim() != 2 or not psf.is_contiguous():
+        raise ValueError("psf must be a contiguous 2-D float32 tensor")
+    img = make_image(src, dst, Params(bits=bits), None, y_out)
+    if workspace is None:
+        workspace = _workspace(wiener_deconv_workspace_size(img.H, img.W), src.device)
+    _check(_lib.wiener_deconvolve(ctypes.byref(img), psf.data_ptr(), int(psf.shape[0]), int(psf.shape[1]),
+                                  float(nsr), _ws_ptr(workspace), _ws_len(workspace), _stream_ptr(stream)),
+           "wiener_deconvolve")
+    return dst
 
 
 # ----------------------------------------------------------------- image parts

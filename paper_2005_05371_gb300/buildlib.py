@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhd.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["hd_kernel.cu", "hd_api.cu", "hd_static.cu", "hd_contrast.cu", "hd_refnoise.cu"]
+SOURCES = ["hd_kernel.cu", "hd_api.cu", "hd_static.cu", "hd_contrast.cu", "hd_refnoise.cu", "hd_fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

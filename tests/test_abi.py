@@ -290,6 +290,34 @@ def test_part_argument_checks():
     assert lib.hybrid_part_apply(ctypes.byref(ok), sums, 0x10010, 1 << 30, None) == hd.HD_ERR_WORKSPACE
 
 
+def test_fourier_wiener_argument_checks():
+    lib = hd._lib
+    S = ctypes.c_size_t
+    n = S()
+    assert lib.wiener_deconv_workspace_size(1620, 1620, ctypes.byref(n)) == hd.HD_OK
+    assert n.value >= 3 * 1620 * 1620 * 8
+    for H, W in ((8192, 8192), (4096, 8), (3000, 4096), (1, 1)):
+        assert lib.wiener_deconv_workspace_size(H, W, ctypes.byref(n)) == hd.HD_OK, (H, W)
+    for H, W in ((16384, 8), (4097, 8), (8, 5000)):
+        assert lib.wiener_deconv_workspace_size(H, W, ctypes.byref(n)) == hd.HD_ERR_OVERFLOW, (H, W)
+    assert lib.wiener_deconv_workspace_size(0, 8, ctypes.byref(n)) == hd.HD_ERR_ARG
+    img = _img(H=16, W=16)
+    ws, big = 0x10000, 1 << 30
+    assert lib.wiener_deconvolve(ctypes.byref(img), None, 3, 3, 0.1, ws, big, None) == hd.HD_ERR_ARG
+    assert lib.wiener_deconvolve(ctypes.byref(img), 0x5002, 3, 3, 0.1, ws, big, None) == hd.HD_ERR_ARG
+    for kh, kw in ((0, 3), (3, 0), (256, 1)):
+        assert lib.wiener_deconvolve(ctypes.byref(img), 0x5000, kh, kw, 0.1, ws, big, None) == hd.HD_ERR_ARG
+    for nsr in (-0.1, float("nan"), float("inf")):
+        assert lib.wiener_deconvolve(ctypes.byref(img), 0x5000, 3, 3, nsr, ws, big, None) == hd.HD_ERR_ARG
+    assert lib.wiener_deconvolve(ctypes.byref(img), 0x5000, 3, 3, 0.1, ws, 10, None) == hd.HD_ERR_WORKSPACE
+    assert lib.wiener_deconvolve(ctypes.byref(_img(H=16, W=5000)), 0x5000, 3, 3, 0.1, ws, big,
+                                 None) == hd.HD_ERR_OVERFLOW
+    assert lib.wiener_deconvolve(ctypes.byref(_img(dtype=hd.HD_U8, bits=9)), 0x5000, 3, 3, 0.1, ws, big,
+                                 None) == hd.HD_ERR_DTYPE
+    assert lib.wiener_deconvolve(ctypes.byref(_img(dst=0x100000 + 8)), 0x5000, 3, 3, 0.1, ws, big,
+                                 None) == hd.HD_ERR_ARG                   # dst overlaps src
+
+
 def test_header_is_plain_c_and_links(tmp_path):
     """The ABI header compiles as C99 (no C++ in its declarations) and a C
     program that takes the address of every entry point links against the
