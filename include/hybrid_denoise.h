@@ -179,8 +179,9 @@ hd_status hd_host_pipeline_submit(hd_host_pipeline *pipeline, const void *src, s
 hd_status hd_host_pipeline_wait(hd_host_pipeline *pipeline);
 hd_status hd_host_pipeline_destroy(hd_host_pipeline *pipeline);
 
-/* The hybrid with the listing's partitioned median (Algorithm 1, step 6:
- * parallelAdapMedian(g, Smax, parts)).  The image is cut into `parts` row
+/* The hybrid with the paper's partitioned median (Algorithm 1, step 6: the
+ * adaptive median of the image in `parts` sub-images, each filtered by its
+ * own worker).  The image is cut into `parts` row
  * strips, strip i covering rows floor(i H / parts) .. floor((i+1) H / parts) - 1,
  * and each strip is median-filtered as an image of its own: its windows
  * reflect at the strip's edges, so pixels within Smax/2 rows of a seam can

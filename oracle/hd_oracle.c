@@ -85,8 +85,9 @@ int oracle_check_smax(int Smax)
  *   keep_unresolved : 0 -> unresolved pixels get zmed(Smax); 1 -> keep zxy
  *   k_out  : optional H x W; the window size at which each pixel passed
  *            level A, or 0 if it never did (diagnostics for the tests)
- * The loops follow the listing: k outermost, then every pixel that is not yet
- * processed ("alreadyProcessed" / t).
+ * Window size k is the outer loop (Section IV: the window grows from 3x3 to
+ * Smax); for each k every pixel that no smaller window has resolved is
+ * tested again (resolved[] marks the others).
  */
 int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
                int keep_unresolved, uint8_t *k_out)
@@ -95,9 +96,9 @@ int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
     if (oracle_check_smax(Smax) != ORACLE_OK) return ORACLE_ERR_SMAX;
 
     long npx = H * W;
-    uint8_t *t = (uint8_t *)calloc((size_t)npx, 1);            /* alreadyProcessed */
+    uint8_t *resolved = (uint8_t *)calloc((size_t)npx, 1);     /* pixel passed level A at some k */
     uint16_t *win = (uint16_t *)malloc((size_t)Smax * Smax * sizeof(uint16_t));
-    if (!t || !win) { free(t); free(win); return ORACLE_ERR_OOM; }
+    if (!resolved || !win) { free(resolved); free(win); return ORACLE_ERR_OOM; }
 
     memcpy(f, g, (size_t)npx * sizeof(uint16_t));              /* f = g */
     if (k_out) memset(k_out, 0, (size_t)npx);
@@ -108,7 +109,7 @@ int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
         for (long y = 0; y < H; ++y) {
             for (long x = 0; x < W; ++x) {
                 long p = y * W + x;
-                if (t[p]) continue;
+                if (resolved[p]) continue;
                 /* k x k neighbourhood of the noisy image g */
                 int m = 0;
                 for (int dy = -r; dy <= r; ++dy) {
@@ -123,11 +124,11 @@ int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
                 uint16_t zmax = win[cnt - 1];
                 uint16_t zmed = win[(cnt - 1) / 2];
                 uint16_t zxy = g[p];
-                int processByLvlB = (zmed > zmin) && (zmax > zmed);       /* level A */
-                if (processByLvlB) {
-                    int zB = (zxy > zmin) && (zmax > zxy);                  /* level B */
-                    f[p] = zB ? zxy : zmed;
-                    t[p] = 1;
+                int level_a = (zmed > zmin) && (zmax > zmed);             /* zmed is not an impulse */
+                if (level_a) {
+                    int level_b = (zxy > zmin) && (zmax > zxy);           /* zxy is not an impulse */
+                    f[p] = level_b ? zxy : zmed;
+                    resolved[p] = 1;
                     if (k_out) k_out[p] = (uint8_t)k;
                 } else if (k == Smax && !keep_unresolved) {
                     f[p] = zmed;                                           /* unresolved */
@@ -135,7 +136,7 @@ int oracle_amf(const uint16_t *g, uint16_t *f, long H, long W, int Smax,
             }
         }
     }
-    free(t);
+    free(resolved);
     free(win);
     return ORACLE_OK;
 }

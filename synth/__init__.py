@@ -5,7 +5,7 @@ is shared by the CUDA path's tests and benchmark and by the oracle's tests,
 so both sides see the same noisy image for the same seed.
 
 The paper (Section V, Fig. 5) ran on a hand X-ray image that is not
-available, and its noise model (Algorithm 1, step 3, ``degradImage``) is only
+available, and its noise model (Algorithm 1, step 3, a degradation step) is only
 named.  The stand-ins below follow the workload shapes of the benchmark
 configurations:
 
