@@ -516,7 +516,7 @@ def run_served(args, rank, world, dev, hd, torch):
             "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
             "config": {**describe("served", items), "requests": n_req, "seconds_of_arrivals": args.served_seconds,
                        "warmup_seconds": 2.0, "megapixels": round(px / 1e6, 1), "parallelism": f"replicas x{world}",
-                       "tuning": {"region_h": tuning[0], "ctas_per_sm": tuning[1]},
+                       "tuning": dict(zip(autotune.FIELDS, tuning)),
                        "l2": f"every request moves its own input/output through HBM (pool {len(items)} images, "
                              f"{sum(h.numel() * h.element_size() for h in hosts) / 1e9:.1f} GB)"},
             "latency": {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
@@ -586,9 +586,11 @@ def main():
     cfg = describe(args.workload, items, args.stretch, args.parts)
     # work-item shape from the autotuner's table (paper_2005_05371_gb300/tuning.json)
     from paper_2005_05371_gb300 import autotune
-    tuning = autotune.choose_batch() if batched else autotune.choose(items[0][0].H, items[0][0].W)
+    s0 = items[0][0]
+    tuning = autotune.choose_batch() if batched else autotune.choose(s0.H, s0.W, s0.dtype, s0.smax, s0.wiener_w,
+                                                                       s0.density)
     hd.hd_set_tuning(*tuning)
-    cfg["tuning"] = {"region_h": tuning[0], "ctas_per_sm": tuning[1]}
+    cfg["tuning"] = dict(zip(autotune.FIELDS, tuning))
     stream = torch.cuda.current_stream(dev)
 
     def to_dev(a):
@@ -625,7 +627,7 @@ def main():
         # with its size class's tuning and a full workspace) on the same data
         ws_plain = [hd._workspace(hd.hybrid_workspace_size(s.H, s.W, code_of(s), params_of(s)), dev)
                     for s, _ in items]
-        slice_tuning = [autotune.choose(s.H, s.W) for s, _ in items]
+        slice_tuning = [autotune.choose(s.H, s.W, s.dtype, s.smax, s.wiener_w, s.density) for s, _ in items]
 
         def plain_step(i, s):
             its = bufs[i % copies]

@@ -1,12 +1,20 @@
-"""Autotuner for the persistent kernel's work-item shape.
+"""Autotuner for the persistent kernel's work-item shape and scheduling knobs.
 
-The tunables are the rows per work item (`region_h`: the median/Wiener region
-is 64 columns x region_h rows) and the grid size in CTAs per SM.  `sweep`
-times every candidate on seeded images of each size class, and on a batch
-plan of uneven slices, with CUDA events over CUDA-graph replays; `tune` keeps
-the fastest per class and writes a JSON table; `choose` / `apply` pick the
-entry for an image at call time and `choose_batch` the one for batches.  Results
-never depend on the tuning (the tests check several shapes), only the speed.
+Knobs (hd_tuning): rows per work item (`region_h`), CTAs per SM, the
+statistics plane (on / off), the one-warp growth cut-over (`small_growth`),
+the lanes sharing one median selection (`select_lanes`) and, for batches,
+the Wiener lag and the image order.  The tile width (64 columns) and the
+threads per CTA (256) are not knobs: each of a warp's 32 lanes owns one pixel
+pair of a region row, and the shared-memory layout is built on that.
+
+Table keys are workload classes: image size class x dtype x Smax class x
+Wiener window class x salt-and-pepper density class (`key`), plus "batch".
+`sweep` tunes each class on two seeded images of it by coordinate descent
+(region height x CTAs per SM, then the growth knobs, then the plane), timing
+CUDA-graph replays with CUDA events; `tune` writes the table; `choose` /
+`choose_batch` pick an entry at call time, falling back to the nearest class
+when the exact one was not tuned.  Results never depend on the tuning (the
+tests check several shapes), only the speed.
 """
 from __future__ import annotations
 
@@ -19,6 +27,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE_PATH = os.path.join(HERE, "tuning.json")
 REGION_H = (16, 24, 32, 40, 48, 56, 64)
 CTAS_PER_SM = (0, 2, 3)
+SMALL_GROWTH = (0, 8, -1)
+SELECT_LANES = (0, 2, 8)
+BATCH_LAG = (3, 6, 10)
+DEFAULT = (32, 0, 0, 0, 0, 0, 0)
+FIELDS = ("region_h", "ctas_per_sm", "plane", "small_growth", "select_lanes", "batch_lag", "batch_order")
 
 
 def size_class(H: int, W: int) -> str:
@@ -30,32 +43,59 @@ def size_class(H: int, W: int) -> str:
     return "large"
 
 
+def smax_class(smax: int) -> str:
+    return "s<=7" if smax <= 7 else "s>=9"
+
+
+def window_class(w: int) -> str:
+    return "w<=3" if w <= 3 else "w>=5"
+
+
+def density_class(density: float | None) -> str:
+    if density is None:
+        return "d?"
+    if density < 0.1:
+        return "d<0.1"
+    if density < 0.3:
+        return "d<0.3"
+    return "d>=0.3"
+
+
+def key(H: int, W: int, dtype: str, smax: int, w: int, density: float | None = None) -> str:
+    return "|".join((size_class(H, W), dtype, smax_class(smax), window_class(w), density_class(density)))
+
+
+# ---------------------------------------------------------------- the classes tuned
 def _cases():
+    """Two seeded images per class: sizes 512^2 / 1620^2 / 4096^2, uint8 and
+    12-bit, Smax 7 / 11 with Wiener 3 / 5, density 0.05 / 0.2 / 0.4."""
     import synth
-    return {
-        "small": [synth.CONFIGS["plain512"]],
-        "medium": [synth.CONFIGS["paper1620"]],
-        "large": [synth.CONFIGS["stress4096"]],
-    }
+    out = {}
+    sizes = {"small": (512, 512), "medium": (1620, 1620), "large": (4096, 4096)}
+    for sc, (H, W) in sizes.items():
+        for dtype, bits, kind in (("u8", 8, "ellipse"), ("u16", 12, "ct")):
+            for smax, w in ((7, 3), (11, 5)):
+                for di, dens in enumerate((0.05, 0.2, 0.4)):
+                    specs = [synth.SliceSpec(H, W, dtype, bits, 20.0 if bits == 8 else 40.0, dens, smax, w,
+                                             9000 + 97 * di + 13 * smax + s, 9500 + 97 * di + 13 * smax + s,
+                                             kind=kind) for s in range(2)]
+                    out[key(H, W, dtype, smax, w, dens)] = specs
+    return out
 
 
-def time_config(hd, torch, spec, g, region_h, ctas, steps=20, warmup=3):
-    """Mean ms per hybrid_denoise launch for one tuning (CUDA-graph replay)."""
-    hd.hd_set_tuning(region_h, ctas)
-    src = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).cuda()
-    dst = torch.empty_like(src)
-    code = hd.HD_U8 if g.dtype == np.uint8 else hd.HD_U16
-    p = hd.Params(spec.smax, spec.wiener_w, bits=spec.bits)
-    ws = hd._workspace(hd.hybrid_workspace_size(spec.H, spec.W, code, p), "cuda")
+def time_images(hd, torch, items, knobs, steps=10):
+    """Mean ms per step (one hybrid_denoise of each image), CUDA-graph replay."""
+    hd.hd_set_tuning(*knobs)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        for _ in range(warmup):
-            hd.hybrid_denoise(src, dst, spec.smax, spec.wiener_w, bits=spec.bits, workspace=ws, stream=s)
+        for src, dst, p, ws in items:
+            hd.hybrid_denoise(src, dst, p.smax, p.wiener_w, bits=p.bits, workspace=ws, stream=s)
     s.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=s):
         for _ in range(steps):
-            hd.hybrid_denoise(src, dst, spec.smax, spec.wiener_w, bits=spec.bits, workspace=ws, stream=s)
+            for src, dst, p, ws in items:
+                hd.hybrid_denoise(src, dst, p.smax, p.wiener_w, bits=p.bits, workspace=ws, stream=s)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(s):
         graph.replay()          # warm
@@ -66,13 +106,13 @@ def time_config(hd, torch, spec, g, region_h, ctas, steps=20, warmup=3):
     return e0.elapsed_time(e1) / steps
 
 
-def time_batch(hd, torch, items, region_h, ctas, launches=10):
-    """Mean ms per launch of a batch plan for one tuning."""
-    hd.hd_set_tuning(region_h, ctas)
+def time_batch(hd, torch, items, knobs, launches=6):
+    """Mean ms per launch of a batch plan."""
+    hd.hd_set_tuning(*knobs)
     plan = hd.BatchPlan(items)
     s = torch.cuda.Stream()
     try:
-        for _ in range(3):
+        for _ in range(2):
             plan.launch(s)
         s.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -87,43 +127,74 @@ def time_batch(hd, torch, items, region_h, ctas, launches=10):
         plan.close()
 
 
-def sweep():
+def _descend(timer, start, axes, log):
+    """Coordinate descent: each group of axes swept in turn around the best so far."""
+    best = list(start)
+    best_ms = timer(tuple(best))
+    log.append({"knobs": list(best), "ms": best_ms})
+    for group in axes:
+        import itertools
+        for values in itertools.product(*[vals for _, vals in group]):
+            k = list(best)
+            for (idx, _), v in zip(group, values):
+                k[idx] = v
+            if k == best:
+                continue
+            ms = timer(tuple(k))
+            log.append({"knobs": k, "ms": ms})
+            if ms < best_ms:
+                best, best_ms = k, ms
+    return tuple(best), best_ms
+
+
+def sweep(classes=None):
+    """{class: {"knobs": [...], "ms": best, "tried": [...]}} for every class."""
     import torch
     import paper_2005_05371_gb300 as hd
     import synth
     old = hd.hd_get_tuning()
     out = {}
     try:
-        for cls, specs in _cases().items():
-            for spec in specs:
-                g = spec.noisy()
-                for rh in REGION_H:
-                    for c in CTAS_PER_SM:
-                        ms = time_config(hd, torch, spec, g, rh, c)
-                        out.setdefault(cls, []).append({"region_h": rh, "ctas_per_sm": c, "ms": ms,
-                                                        "H": spec.H, "W": spec.W})
-        # batches: 64 uneven 12-bit slices of the batched workload's kind
-        items = []
-        for sp in synth.batch_specs(64, master_seed=400):
-            src = torch.from_numpy(sp.noisy().view(np.int16)).cuda()
-            items.append((src, torch.empty_like(src), hd.Params(sp.smax, sp.wiener_w, -1.0, 0, 0, sp.bits)))
-        for rh in REGION_H:
-            for c in CTAS_PER_SM:
-                out.setdefault("batch", []).append({"region_h": rh, "ctas_per_sm": c,
-                                                    "ms": time_batch(hd, torch, items, rh, c), "images": 64})
+        cases = _cases()
+        for k, specs in cases.items():
+            if classes and k not in classes:
+                continue
+            items = []
+            for sp in specs:
+                g = sp.noisy()
+                src = torch.from_numpy(g.view(np.int16) if g.dtype == np.uint16 else g).cuda()
+                p = hd.Params(sp.smax, sp.wiener_w, bits=sp.bits)
+                code = hd.HD_U8 if sp.dtype == "u8" else hd.HD_U16
+                ws = hd._workspace(hd.hybrid_workspace_size(sp.H, sp.W, code, p), "cuda")
+                items.append((src, torch.empty_like(src), p, ws))
+            log = []
+            axes = [[(0, REGION_H), (1, CTAS_PER_SM)], [(3, SMALL_GROWTH), (4, SELECT_LANES)], [(2, (0, 1))]]
+            best, ms = _descend(lambda kn: time_images(hd, torch, items, kn), (56, 3, 0, 0, 0, 0, 0), axes, log)
+            out[k] = {"knobs": list(best), "ms": ms, "images": [[sp.H, sp.W] for sp in specs], "tried": log}
+            del items
+            torch.cuda.empty_cache()
+        if not classes or "batch" in classes:
+            items = []
+            for seed in (400, 401):
+                for sp in synth.batch_specs(32, master_seed=seed):
+                    src = torch.from_numpy(sp.noisy().view(np.int16)).cuda()
+                    items.append((src, torch.empty_like(src), hd.Params(sp.smax, sp.wiener_w, -1.0, 0, 0, sp.bits)))
+            log = []
+            axes = [[(0, REGION_H), (1, CTAS_PER_SM)], [(5, BATCH_LAG), (6, (0, 1))],
+                    [(3, SMALL_GROWTH), (4, SELECT_LANES)]]
+            best, ms = _descend(lambda kn: time_batch(hd, torch, items, kn), (64, 3, 0, 0, 0, 6, 0), axes, log)
+            out["batch"] = {"knobs": list(best), "ms": ms, "images": len(items), "tried": log}
     finally:
         hd.hd_set_tuning(*old)
     return out
 
 
-def tune(path: str = TABLE_PATH):
-    res = sweep()
-    table = {}
-    for cls, rows in res.items():
-        best = min(rows, key=lambda r: r["ms"])
-        table[cls] = {"region_h": best["region_h"], "ctas_per_sm": best["ctas_per_sm"], "ms": best["ms"]}
+def tune(path: str = TABLE_PATH, classes=None):
+    res = sweep(classes)
+    table = {k: {"knobs": v["knobs"], "ms": v["ms"]} for k, v in res.items()}
     with open(path, "w") as fh:
-        json.dump({"table": table, "sweep": res}, fh, indent=1)
+        json.dump({"fields": list(FIELDS), "table": table, "sweep": res}, fh, indent=1)
+    _loaded.pop(path, None)
     return table
 
 
@@ -141,27 +212,46 @@ def _table(path: str) -> dict:
     return _loaded[path]
 
 
-def choose(H: int, W: int, path: str = TABLE_PATH):
-    """(region_h, ctas_per_sm) for an image, from the tuned table (default (32, 0))."""
-    ent = _table(path).get(size_class(H, W))
-    if not ent:
-        return 32, 0
-    return int(ent["region_h"]), int(ent["ctas_per_sm"])
+def _knobs(ent) -> tuple:
+    k = tuple(int(x) for x in ent["knobs"])
+    return k + DEFAULT[len(k):]
 
 
-def choose_batch(path: str = TABLE_PATH):
-    """(region_h, ctas_per_sm) for batched launches (default: the large-image entry)."""
+def choose(H: int, W: int, dtype: str = "u8", smax: int = 9, w: int = 5, density: float | None = None,
+           path: str = TABLE_PATH) -> tuple:
+    """hd_set_tuning arguments for an image: the tuned entry of its class or
+    of the nearest tuned class (same size and dtype first, then the same
+    size); the library's defaults when nothing of its size was tuned."""
+    tab = _table(path)
+    k = key(H, W, dtype, smax, w, density)
+    if k in tab:
+        return _knobs(tab[k])
+    size, dt, sc, wc, dc = k.split("|")
+    # the density class a caller did not give: the middle one
+    for cand in (f"{size}|{dt}|{sc}|{wc}|d<0.3", f"{size}|{dt}|{sc}|{wc}|d<0.1", f"{size}|{dt}|{sc}|{wc}|d>=0.3"):
+        if cand in tab:
+            return _knobs(tab[cand])
+    same = [v for kk, v in tab.items() if kk.startswith(f"{size}|{dt}|")] or \
+        [v for kk, v in tab.items() if kk.startswith(f"{size}|")]
+    if same:
+        return _knobs(min(same, key=lambda v: v["ms"]))
+    return DEFAULT
+
+
+def choose_batch(path: str = TABLE_PATH) -> tuple:
+    """hd_set_tuning arguments for batched launches (default: the large-image entry)."""
     ent = _table(path).get("batch")
     if not ent:
-        return choose(4096, 4096, path)
-    return int(ent["region_h"]), int(ent["ctas_per_sm"])
+        return choose(4096, 4096, "u16", 11, 5, None, path)
+    return _knobs(ent)
 
 
-def apply(H: int, W: int):
-    """Set the library's tuning for an H x W image from the table."""
+def apply(H: int, W: int, dtype: str = "u8", smax: int = 9, w: int = 5, density: float | None = None):
+    """Set the library's tuning for an image of this class from the table."""
     import paper_2005_05371_gb300 as hd
-    hd.hd_set_tuning(*choose(H, W))
+    hd.hd_set_tuning(*choose(H, W, dtype, smax, w, density))
 
 
 if __name__ == "__main__":
-    print(json.dumps(tune(), indent=1))
+    import sys
+    print(json.dumps(tune(classes=sys.argv[1:] or None), indent=1))
