@@ -210,6 +210,9 @@ def weak_value(px_per_rank: int, steps: int, max_ms: float, world: int) -> float
 SERVED_POOL = 256
 
 
+BATCH_SLICES = 256
+
+
 def workload_specs(name: str, rank: int):
     """The seeded specs of a workload.  Rank r draws its own replica (distinct seeds)."""
     import synth
@@ -220,7 +223,7 @@ def workload_specs(name: str, rank: int):
                                       "noise_seed": spec.noise_seed + 1000 * rank})
         return [spec]
     if name == "batched":
-        return synth.batch_specs(256, master_seed=400 + rank)
+        return synth.batch_specs(256, master_seed=400 + rank)[:BATCH_SLICES]
     if name == "served":
         return synth.served_specs(SERVED_POOL, seed=501 + rank)
     raise SystemExit(f"unknown workload {name}")
@@ -555,9 +558,17 @@ def main():
                     help="row strips of the partitioned median (Algorithm 1, step 6); 1 = whole image")
     ap.add_argument("--stretch", type=float, default=None,
                     help="also run the contrast stretch (Algorithm 1, step 4e) with this tolerance every step")
+    ap.add_argument("--slices", type=int, default=256,
+                    help="batched: the first N slices of the 256 (smaller cases for profiling)")
+    ap.add_argument("--fourier", type=float, default=None,
+                    help="single image: also time the Wiener filter in the Fourier domain (wiener_deconvolve, "
+                         "7x7 Gaussian PSF) with this noise-to-signal ratio")
     args = ap.parse_args()
-    if (args.stretch is not None or args.parts > 1) and args.workload in ("batched", "served"):
-        raise SystemExit("--stretch and --parts apply to the single-image workloads")
+    global BATCH_SLICES
+    BATCH_SLICES = max(1, min(256, args.slices))
+    if (args.stretch is not None or args.parts > 1 or args.fourier is not None) and \
+            args.workload in ("batched", "served"):
+        raise SystemExit("--stretch, --parts and --fourier apply to the single-image workloads")
     if args.parts < 1:
         raise SystemExit("--parts must be >= 1")
     if args.warmup < 3:
@@ -777,6 +788,38 @@ def main():
         status = hd.hd_get_device_error(stream)
         if status != hd.HD_OK:
             raise SystemExit(f"device error in the per-kernel timing: {hd.hd_status_str(status)}")
+    if args.fourier is not None:
+        # the Wiener filter in the Fourier domain alone (Section IV), same image
+        # rotation; its traffic counts the binary32 complex planes (8 bytes a
+        # pixel) each pass reads or writes: 5 for the PSF's transfer function
+        # (row pass, transpose, column pass) and 9 for the image (row pass,
+        # transpose, filtered column pass reading the PSF's plane too,
+        # transpose, inverse row pass)
+        r = np.arange(7) - 3
+        kern = np.exp(-(r[:, None] ** 2 + r[None, :] ** 2) / (2 * 1.5 * 1.5))
+        psf = torch.from_numpy((kern / kern.sum()).astype(np.float32)).to(dev)
+        fws = hd._workspace(hd.wiener_deconv_workspace_size(spec.H, spec.W), dev)
+        fdsts = [torch.empty_like(srcs[0]) for _ in range(copies)]
+
+        def fourier_step(i, s):
+            j = i % copies
+            hd.wiener_deconvolve(srcs[j], fdsts[j], psf, args.fourier, bits=p.bits, workspace=fws, stream=s)
+        K2 = max(10, args.steps)
+        f_ms, _, _ = timed(fourier_step, K2, args.warmup, True)
+        f_ms = max_over_ranks(f_ms, dev) / K2
+        plane_traffic = 14 * spec.H * spec.W * 8
+        f_ach = plane_traffic / (f_ms / 1e3) / 1e9
+        extra["fourier_wiener"] = {"kernels": "fft_rows_kernel, fft_transpose_kernel, fft_tables_kernel",
+                                   "ms": round(f_ms, 5), "mpixel_s": round(px_per_step / (f_ms / 1e3) / 1e6, 1),
+                                   "nsr": args.fourier, "psf": "7x7 Gaussian, sigma 1.5",
+                                   "bound": "hbm", "achieved": round(f_ach, 1), "peak": peak, "unit": "GB/s",
+                                   "frac": round(f_ach / peak, 4), "bytes_per_call": plane_traffic,
+                                   "bytes_note": "14 reads or writes of an H x W binary32 complex plane "
+                                                 "(8 bytes a pixel)",
+                                   "launches_per_call": 10}
+        status = hd.hd_get_device_error(stream)
+        if status != hd.HD_OK:
+            raise SystemExit(f"device error in the Fourier-domain Wiener: {hd.hd_status_str(status)}")
     achieved = step_bytes / (hybrid_ms / 1e3) / 1e9
     # the integer/FP32 side of the roofline: algorithmic operations per pixel
     # of the 3x3 median stage and the Wiener stage (window growth not
