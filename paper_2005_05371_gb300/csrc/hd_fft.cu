@@ -5,8 +5,9 @@
 // with the 2-D DFT's periodic extension as the border rule and
 // out = min(maxv, floor(y + 1/2)) (negatives to 0).
 //
-// The 2-D DFT is a row pass and a column pass of 1-D DFTs.  One CTA
-// transforms one row held whole in shared memory (binary32 complex):
+// The 2-D DFT is a row pass and a column pass of 1-D DFTs.  A CTA transforms
+// 8192 / M rows at once, each held whole in shared memory (binary32 complex),
+// with the twiddles staged in shared memory per stage:
 //   - a power-of-two length M: radix-2 in place, decimation in time from
 //     bit-reversed input to natural output (forward and inverse alike;
 //     the inverse conjugates the twiddles);
@@ -92,15 +93,18 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 __device__ __forceinline__ int bitrev(int k, int logM) { return (int)(__brev((u32)k) >> (32 - logM)); }
 
 // Radix-2 decimation in time: bit-reversed input, natural output.  The
-// butterfly of span h at position p uses exp(-+2 pi i p / (2h)) = tw[p M / (2h)].
-__device__ void fft_dit(float2 *x, int M, int logM, const float2 *tw, bool inverse)
+// butterfly of span h at position p uses exp(-+2 pi i p / (2h)), which sits
+// at ts[h - 1 + p] of the per-stage table in shared memory (consecutive
+// positions at consecutive entries: no bank conflicts).  lt and T: this
+// thread's index within its row group and the group's size.
+__device__ void fft_dit(float2 *x, int M, int logM, const float2 *ts, bool inverse, int lt, int T)
 {
     for (int s = 1; s <= logM; ++s) {
-        const int half = 1 << (s - 1), step = M >> s;
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
+        const int half = 1 << (s - 1);
+        for (int b = lt; b < (M >> 1); b += T) {
             const int pos = b & (half - 1);
             const int i = ((b >> (s - 1)) << s) + pos, j = i + half;
-            float2 w = __ldg(&tw[pos * step]);
+            float2 w = ts[half - 1 + pos];
             if (inverse) w.y = -w.y;
             const float2 u = x[i], v = cmul(w, x[j]);
             x[i] = make_float2(u.x + v.x, u.y + v.y);
@@ -111,14 +115,14 @@ __device__ void fft_dit(float2 *x, int M, int logM, const float2 *tw, bool inver
 }
 
 // Radix-2 decimation in frequency: natural input, bit-reversed output.
-__device__ void fft_dif(float2 *x, int M, int logM, const float2 *tw, bool inverse)
+__device__ void fft_dif(float2 *x, int M, int logM, const float2 *ts, bool inverse, int lt, int T)
 {
     for (int s = logM; s >= 1; --s) {
-        const int half = 1 << (s - 1), step = M >> s;
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
+        const int half = 1 << (s - 1);
+        for (int b = lt; b < (M >> 1); b += T) {
             const int pos = b & (half - 1);
             const int i = ((b >> (s - 1)) << s) + pos, j = i + half;
-            float2 w = __ldg(&tw[pos * step]);
+            float2 w = ts[half - 1 + pos];
             if (inverse) w.y = -w.y;
             const float2 u = x[i], v = x[j];
             x[i] = make_float2(u.x + v.x, u.y + v.y);
@@ -130,39 +134,40 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *tw, bool inver
 
 // x[k] -> x[bitrev(k)] for k < M, through registers (every thread holds at
 // most kStageElems entries).
-__device__ void bitrev_inplace(float2 *x, int M, int logM)
+__device__ void bitrev_inplace(float2 *x, int M, int logM, int lt, int T)
 {
     float2 v[kStageElems];
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         if (k < M) v[i] = x[k];
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         if (k < M) x[bitrev(k, logM)] = v[i];
     }
     __syncthreads();
 }
 
 // Unscaled DFT of x[0, N) in shared memory, in place, natural order in and
-// out: sum_n x_n exp(-+2 pi i n k / N) (sign + for the inverse).
-__device__ void dft_row(float2 *x, const LenTables &t, bool inverse)
+// out: sum_n x_n exp(-+2 pi i n k / N) (sign + for the inverse); ts is the
+// per-stage twiddle table of t.M in shared memory (see fft_dit).
+__device__ void dft_row(float2 *x, const LenTables &t, const float2 *ts, bool inverse, int lt, int T)
 {
     const int N = t.N, M = t.M, logM = t.logM;
     if (M == 1) return;
     if (M == N) {
-        bitrev_inplace(x, M, logM);
-        fft_dit(x, M, logM, t.tw, inverse);
+        bitrev_inplace(x, M, logM, lt, T);
+        fft_dit(x, M, logM, ts, inverse, lt, T);
         return;
     }
     // Bluestein; the inverse through conjugation: IDFT(x) = conj(DFT(conj(x)))
     float2 v[kStageElems];
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         float2 a = make_float2(0.f, 0.f);
         if (k < N) {
             a = x[k];
@@ -174,25 +179,25 @@ __device__ void dft_row(float2 *x, const LenTables &t, bool inverse)
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         if (k < M) x[bitrev(k, logM)] = v[i];
     }
     __syncthreads();
-    fft_dit(x, M, logM, t.tw, false);
-    for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cmul(x[k], __ldg(&t.bhat[k]));
+    fft_dit(x, M, logM, ts, false, lt, T);
+    for (int k = lt; k < M; k += T) x[k] = cmul(x[k], __ldg(&t.bhat[k]));
     __syncthreads();
-    fft_dif(x, M, logM, t.tw, true);
+    fft_dif(x, M, logM, ts, true, lt, T);
     // X_k = w_k c_k / M, c in bit-reversed order
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         if (k < N) v[i] = x[bitrev(k, logM)];
     }
     __syncthreads();
     const float inv_m = 1.0f / (float)M;
 #pragma unroll
     for (int i = 0; i < kStageElems; ++i) {
-        const int k = threadIdx.x + i * blockDim.x;
+        const int k = lt + i * T;
         if (k < N) {
             float2 r = cmul(v[i], __ldg(&t.chirp[k]));
             r.x *= inv_m;
@@ -204,57 +209,83 @@ __device__ void dft_row(float2 *x, const LenTables &t, bool inverse)
     __syncthreads();
 }
 
-// One CTA per row (grid-stride): load, transform, store.
+// Rows per CTA for a transform length M: the CTA's 1024 threads split into
+// groups of 1024 / R, each transforming one row in its own M entries of
+// shared memory (R M <= kMaxM, so every thread stages at most kStageElems).
+__host__ __device__ inline int rows_per_cta(int M) { return M >= kMaxM ? 1 : (kMaxM / M < 64 ? kMaxM / M : 64); }
+
+// R rows per CTA (grid-stride over row groups): load, transform, store.
+// Every group runs the same transform (same length and operation).  A group
+// can be narrower than a warp, so one warp may hold a row and a group past
+// the last row: every block-wide barrier therefore sits where all threads of
+// the CTA reach it, behind conditions that are the same for the whole CTA.
+// A group past the last row transforms zeros and stores nothing.
 __global__ void __launch_bounds__(kFftThreads) fft_rows_kernel(const __grid_constant__ RowParams p)
 {
-    extern __shared__ float2 xs[];
-    const int N = p.t.N;
-    for (int r = blockIdx.x; r < p.rows; r += gridDim.x) {
-        if (p.load == LOAD_IMAGE) {
-            const uint8_t *row = p.img + (long long)r * p.img_pitch;
-            for (int k = threadIdx.x; k < N; k += blockDim.x) {
-                const u32 v = p.elem == 1 ? (u32)row[k] : (u32)reinterpret_cast<const u16 *>(row)[k];
-                xs[k] = make_float2((float)v, 0.f);
-            }
-        } else if (p.load == LOAD_COMPLEX) {
-            const float2 *row = p.in + (long long)r * p.in_stride;
-            for (int k = threadIdx.x; k < N; k += blockDim.x) xs[k] = row[k];
-        } else {
-            // the PSF's taps that land on grid row r, scattered onto the row's columns
-            for (int k = threadIdx.x; k < N; k += blockDim.x) xs[k] = make_float2(0.f, 0.f);
-            __syncthreads();
-            const int taps = p.kh * p.kw;
-            for (int q = threadIdx.x; q < taps; q += blockDim.x) {
-                const int i = q / p.kw, j = q - i * p.kw;
-                int gr = (i - p.kh / 2) % p.grid_rows;
-                if (gr < 0) gr += p.grid_rows;
-                if (gr != r) continue;
-                int gc = (j - p.kw / 2) % N;
-                if (gc < 0) gc += N;
-                atomicAdd(&xs[gc].x, p.psf[q]);
+    extern __shared__ float2 xs_all[];
+    const int N = p.t.N, M = p.t.M;
+    const int R = rows_per_cta(M), T = kFftThreads / R;
+    const int grp = threadIdx.x / T, lt = threadIdx.x - grp * T;
+    float2 *xs = xs_all + (size_t)grp * M;
+    // the per-stage twiddle table: stage s (span h = 2^(s-1)) holds
+    // exp(-2 pi i p / (2h)) = tw[p M / (2h)] for p < h at entries h - 1 + p
+    float2 *ts = xs_all + (size_t)R * M;
+    for (int e = threadIdx.x; e < M - 1; e += blockDim.x) {
+        const int h = 1 << (31 - __clz(e + 1));
+        ts[e] = __ldg(&p.t.tw[(e + 1 - h) * (M / (2 * h))]);
+    }
+    __syncthreads();
+    for (int r0 = blockIdx.x * R; r0 < p.rows; r0 += gridDim.x * R) {
+        const int r = r0 + grp;
+        const bool live = r < p.rows;
+        if (p.load == LOAD_PSF || !live)
+            for (int k = lt; k < N; k += T) xs[k] = make_float2(0.f, 0.f);
+        if (p.load == LOAD_PSF) __syncthreads();
+        if (live) {
+            if (p.load == LOAD_IMAGE) {
+                const uint8_t *row = p.img + (long long)r * p.img_pitch;
+                for (int k = lt; k < N; k += T) {
+                    const u32 v = p.elem == 1 ? (u32)row[k] : (u32)reinterpret_cast<const u16 *>(row)[k];
+                    xs[k] = make_float2((float)v, 0.f);
+                }
+            } else if (p.load == LOAD_COMPLEX) {
+                const float2 *row = p.in + (long long)r * p.in_stride;
+                for (int k = lt; k < N; k += T) xs[k] = row[k];
+            } else {
+                // the PSF's taps that land on grid row r, scattered onto the row's columns
+                const int taps = p.kh * p.kw;
+                for (int q = lt; q < taps; q += T) {
+                    const int i = q / p.kw, j = q - i * p.kw;
+                    int gr = (i - p.kh / 2) % p.grid_rows;
+                    if (gr < 0) gr += p.grid_rows;
+                    if (gr != r) continue;
+                    int gc = (j - p.kw / 2) % N;
+                    if (gc < 0) gc += N;
+                    atomicAdd(&xs[gc].x, p.psf[q]);
+                }
             }
         }
         __syncthreads();
         if (p.op == OP_FILTER) {
-            dft_row(xs, p.t, false);
+            dft_row(xs, p.t, ts, false, lt, T);
             // conj(P) / (|P|^2 + nsr)
-            const float2 *ps = p.pspec + (long long)r * p.pspec_stride;
-            for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const float2 *ps = p.pspec + (long long)(live ? r : 0) * p.pspec_stride;
+            for (int k = lt; k < N; k += T) {
                 const float2 P = ps[k];
                 const float den = P.x * P.x + P.y * P.y + p.nsr;
                 xs[k] = cmul(xs[k], make_float2(P.x / den, -P.y / den));
             }
             __syncthreads();
-            dft_row(xs, p.t, true);
+            dft_row(xs, p.t, ts, true, lt, T);
         } else {
-            dft_row(xs, p.t, p.op == OP_INV);
+            dft_row(xs, p.t, ts, p.op == OP_INV, lt, T);
         }
-        if (p.store == STORE_COMPLEX) {
+        if (live && p.store == STORE_COMPLEX) {
             float2 *row = p.out + (long long)r * p.out_stride;
-            for (int k = threadIdx.x; k < N; k += blockDim.x) row[k] = xs[k];
-        } else {
+            for (int k = lt; k < N; k += T) row[k] = xs[k];
+        } else if (live) {
             uint8_t *row = p.dst + (long long)r * p.dst_pitch;
-            for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            for (int k = lt; k < N; k += T) {
                 const float y = xs[k].x * p.scale;
                 if (p.y_out) p.y_out[(long long)r * N + k] = y;
                 // floor(y + 0.5) clamped to [0, maxv]: the round-down conversion
@@ -385,13 +416,16 @@ cudaError_t launch_rows(const RowParams &p, cudaStream_t s)
         std::lock_guard<std::mutex> lk(g_attr_mu);
         if (!g_attr_set) {
             const cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)(kMaxM * sizeof(float2)));
+                                                       (int)(2 * kMaxM * sizeof(float2)));
             if (e != cudaSuccess) return e;
             g_attr_set = true;
         }
     }
-    const int grid = std::min(p.rows, 65535);
-    fft_rows_kernel<<<grid, kFftThreads, (size_t)p.t.M * sizeof(float2), s>>>(p);
+    const int R = rows_per_cta(p.t.M);
+    const int grid = std::min((p.rows + R - 1) / R, 65535);
+    // R rows, then the per-stage twiddle table (M - 1 entries)
+    const size_t smem = ((size_t)R * p.t.M + (size_t)p.t.M) * sizeof(float2);
+    fft_rows_kernel<<<grid, kFftThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
