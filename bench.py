@@ -241,7 +241,7 @@ def describe(name: str, items, stretch: float | None = None, parts: int = 1) -> 
     if name == "served":
         return {"workload": f"served: Poisson 2000 req/s over a pool of {len(items)} seeded phantoms, side "
                             "log-uniform [512, 4096], u8 / 12-bit 50/50, s&p up to 0.3, Smax {5..11}, Wiener "
-                            "{3,5,7}, 8 GB device budget, continuous batching (3 rounds in flight)",
+                            "{3,5,7}, 8 GB device budget, continuous batching",
                 "images": len(items), "megapixels": round(px / 1e6, 3)}
     if name == "batched":
         return {"workload": "batched: 256 uneven 12-bit slices {256^2,512^2,768x512,1024^2}, sigma U[10,60], "
@@ -469,7 +469,7 @@ def run_served(args, rank, world, dev, hd, torch):
                       "p99_ms": round(float(np.percentile(lat, 99)), 3), "mpixel_s": round(px / span / 1e6, 1),
                       "requests": len(reqs)}
 
-    srv = Server(budget_bytes=8 << 30, max_inflight=3, device=dev)
+    srv = Server(budget_bytes=8 << 30, max_inflight=max(1, args.inflight), device=dev)
     try:
         run(srv, rate, 2.0, 499)                            # warm-up: 2 s of arrivals
         srv.finished.clear()
@@ -518,6 +518,7 @@ def run_served(args, rank, world, dev, hd, torch):
             "warmup": int(rate * 2.0), "ms_per_step": round(span_ms / n_req, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
             "config": {**describe("served", items), "requests": n_req, "seconds_of_arrivals": args.served_seconds,
+                       "rounds_in_flight": max(1, args.inflight),
                        "warmup_seconds": 2.0, "megapixels": round(px / 1e6, 1), "parallelism": f"replicas x{world}",
                        "tuning": dict(zip(autotune.FIELDS, tuning)),
                        "l2": f"every request moves its own input/output through HBM (pool {len(items)} images, "
@@ -552,6 +553,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of single-thread oracle work")
     ap.add_argument("--ref-budget", type=float, default=90.0, help="total seconds of the reference arm")
     ap.add_argument("--served-seconds", type=float, default=10.0, help="seconds of arrivals of the served run")
+    ap.add_argument("--inflight", type=int, default=3, help="served: rounds in flight on the device at once")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--parts", type=int, default=1,

@@ -428,7 +428,12 @@ hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pipeline);
  *   region_h:     multiple of 8 in [16, 128] (default 32).
  *   ctas_per_sm:  grid size per SM, 1..8, 0 = as many as fit.
  *   plane:        0 = a single image uses the statistics plane whenever its
- *                 workspace has room for it; 1 = never (recompute pass).
+ *                 workspace has room for it, its Wiener pass reading the
+ *                 plane straight from L2 when the plane, the median output
+ *                 and the output of the image fit in half of the L2, else
+ *                 staging it in shared memory by bulk copies; 1 = never
+ *                 (recompute pass); 2 = the plane, always staged; 3 = the
+ *                 plane, always read straight from L2.
  *   small_growth: when at most this many pixels of a region fail level A at
  *                 3x3, one warp grows their windows with no block barriers:
  *                 0 = default (32), -1 = never, 1..32.

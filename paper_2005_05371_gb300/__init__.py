@@ -648,7 +648,8 @@ def hd_set_tuning(region_h: int = 32, ctas_per_sm: int = 0, plane: int = 0, smal
                   select_lanes: int = 0, batch_lag: int = 0, batch_order: int = 0):
     """Work-item shape and scheduling knobs (see hd_tuning in the header):
     rows per work item (multiple of 8 in [16, 128]), CTAs per SM (0 = all that
-    fit), statistics plane (0 = when there is room, 1 = never), one-warp growth
+    fit), statistics plane (0 = when there is room, its Wiener pass read from
+    L2 or staged by the working set; 1 = never; 2 = staged; 3 = from L2), one-warp growth
     cut-over (0 = 32, -1 = never), lanes per median selection (0, 1, 2, 4, 8),
     batch Wiener lag in grids (0 = 6) and batch order (0 = the caller's, 1 = largest first)."""
     t = hd_tuning(region_h, ctas_per_sm, plane, small_growth, select_lanes, batch_lag, batch_order)

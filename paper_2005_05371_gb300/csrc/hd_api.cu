@@ -104,6 +104,22 @@ int device_sms()
     return cache[dev];
 }
 
+size_t device_l2_bytes()
+{
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, -1);
+    if (cache[dev] < 0) {
+        int b = 0;
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev) != cudaSuccess) b = 0;
+        cache[dev] = b;
+    }
+    return (size_t)cache[dev];
+}
+
 size_t f_pitch_of(int W, int dtype) { return round_up((size_t)W * elem_size(dtype), 16); }
 
 // Workspace layout of a single image: [ticket][ImgCtl] [fbuf] [plane].  The
@@ -197,7 +213,15 @@ hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t 
     int per_sm = max_ctas_per_sm(*smem);
     if (per_sm <= 0) return HD_ERR_CUDA;
     if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
-    // plane mode: every resident CTA takes a share of the phase-2 pixels
+    // plane mode: every resident CTA takes a share of the phase-2 pixels,
+    // read straight from L2 when the plane, f and the output of the owned rows
+    // fit in half of it (they were written moments before), else staged by
+    // bulk copies, which keep more bytes in flight from HBM
+    if (lp.p2_plane) {
+        const ImgDesc &d = lp.one;
+        const size_t px = (size_t)(d.own1 - d.own0) * (size_t)d.W;
+        lp.p2_direct = t.plane == 3 || (t.plane != 2 && px * (8 + 2 * (size_t)d.elem) <= device_l2_bytes() / 2);
+    }
     *grid = std::max(1, lp.p2_plane ? sms * per_sm : std::min(lp.total_items, sms * per_sm));
     return HD_OK;
 }
@@ -219,7 +243,7 @@ hd_status run_single(const hd_image *img, int mode, void *ws, size_t ws_bytes, c
         ticket = static_cast<unsigned int *>(ws);
         ctl = reinterpret_cast<ImgCtl *>(static_cast<uint8_t *>(ws) + kTicketBytes);
         if (needs_fbuf) fbuf = static_cast<uint8_t *>(ws) + ctl_bytes();
-        if (t.plane == 0 && ws_bytes >= need + plane_bytes(img->H, img->W))
+        if (t.plane != 1 && ws_bytes >= need + plane_bytes(img->H, img->W))
             plane = reinterpret_cast<float *>(static_cast<uint8_t *>(ws) + need);
     }
     LaunchParams lp;
@@ -1303,7 +1327,7 @@ hd_status hd_set_tuning(const hd_tuning *t)
     if (!t) return HD_ERR_ARG;
     if (t->region_h < 16 || t->region_h > 128 || (t->region_h % 8) != 0) return HD_ERR_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 8) return HD_ERR_ARG;
-    if (t->plane < 0 || t->plane > 1) return HD_ERR_ARG;
+    if (t->plane < 0 || t->plane > 3) return HD_ERR_ARG;
     if (t->small_growth < -1 || t->small_growth > 32) return HD_ERR_ARG;
     if (t->select_lanes != 0 && t->select_lanes != 1 && t->select_lanes != 2 && t->select_lanes != 4 &&
         t->select_lanes != 8)

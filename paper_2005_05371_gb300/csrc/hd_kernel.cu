@@ -71,7 +71,7 @@ __device__ unsigned int g_device_error;
 // of every CTA adds the clock cycles between consecutive stamps to
 // g_stage_cycles[stage].  Compiled out otherwise.
 #ifdef HD_STAGE_PROFILE
-__device__ unsigned long long g_stage_cycles[16];
+__device__ unsigned long long g_stage_cycles[32];
 #define HD_STAMP_INIT() long long hd_t0_ = clock64()
 #define HD_STAMP(i)                                                                  \
     do {                                                                             \
@@ -81,9 +81,28 @@ __device__ unsigned long long g_stage_cycles[16];
             hd_t0_ = t_;                                                             \
         }                                                                            \
     } while (0)
+// Per-CTA global timestamps (ns): kernel start, end of the ticket loop, end
+// of the phase-2 wait, end; and the number of items the CTA ran.
+__device__ unsigned long long g_cta_t[4096][5];
+__device__ __forceinline__ unsigned long long hd_gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define HD_CTA_T(i)                                                                  \
+    do {                                                                             \
+        if (threadIdx.x == 0 && blockIdx.x < 4096) g_cta_t[blockIdx.x][i] = hd_gtime(); \
+    } while (0)
+#define HD_CTA_ITEMS(n)                                                              \
+    do {                                                                             \
+        if (threadIdx.x == 0 && blockIdx.x < 4096) g_cta_t[blockIdx.x][4] = (n);    \
+    } while (0)
 #else
 #define HD_STAMP_INIT() (void)0
 #define HD_STAMP(i) (void)0
+#define HD_CTA_T(i) (void)0
+#define HD_CTA_ITEMS(n) (void)0
 #endif
 
 namespace {
@@ -1149,6 +1168,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
 {
     const int w = d.w, wy = d.wh;      // window columns, rows
     constexpr bool with_plane = PLANE;
+    HD_STAMP_INIT();
     hsums<NARROW>(g, fs, H1, h2p, w, with_plane);
     const bool zero = d.border_zero != 0;
     const int gy0 = g.y0 + d.gy_off;       // the tile's first row in the whole image
@@ -1161,6 +1181,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         }
     }
     __syncthreads();
+    HD_STAMP(16);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = 2 * lane;
     const int per = (g.th + kWarps - 1) / kWarps;
@@ -1248,6 +1269,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
             }
         }
     }
+    HD_STAMP(17);
     if (interior) accB *= (u64)w * (u64)wy;
     accA = warp_sum_u64(accA);
     accB = warp_sum_u64(accB);
@@ -1256,6 +1278,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
         bs.red[1][warp] = accB;
     }
     __syncthreads();
+    HD_STAMP(18);
     if (threadIdx.x == 0) {
         u64 sa = 0, sb = 0;
         for (int i = 0; i < kWarps; ++i) {
@@ -1313,11 +1336,12 @@ __device__ __forceinline__ u32 wiener_ms(float mu, float s2, u32 fv, const Apply
 // ---------------------------------------------------------------- plane-mode phase 2
 // Every CTA applies its own contiguous share of the image's pixels (all CTAs
 // reach phase 2 together, at the image-wide barrier, so equal shares are
-// balanced), in units of up to kUnitPx pixels staged in shared memory by bulk
-// copies (cp.async.bulk, completion counted on an mbarrier per stage) up to
-// kStages units ahead of the one being applied.  Thread 0 issues the copies;
-// all threads apply; a block barrier per unit frees its stage for the next
-// copy.
+// balanced).  Two ways, chosen on the host by the working set: straight from
+// L2 (p2_direct, below), or in units of up to kUnitPx pixels staged in shared
+// memory by bulk copies (cp.async.bulk, completion counted on an mbarrier per
+// stage) up to kStages units ahead of the one being applied (p2_share).
+// There thread 0 issues the copies; all threads apply; a block barrier per
+// unit frees its stage for the next copy.
 __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(u64 *m, u32 count)
@@ -1701,13 +1725,175 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
     HD_STAMP(6);
 }
 
-// One phase-2 slot of a plane-mode image (all threads of the CTA): stream
-// units until the image has none left.
+// Plane-mode phase 2 read straight from L2: the CTA's share of image d is
+// pixels [pb, pe) of the row-major order (the gridDim.x shares equal up to a
+// pixel pair, each starting an even distance after the first owned pixel, so
+// that a group's (mu, s2) pairs start on a 16-byte boundary).  Thread t
+// applies the 4-pixel groups t, t + kThreads, ... of the share; the loads of
+// a thread's next group are issued before the arithmetic of its current one,
+// and no block barrier is taken after the noise variance is known.
+struct P2Group {
+    float4 a, b;      // (mu, s2) of pixels 0, 1 and of pixels 2, 3
+    u32 f[4];         // f of the four pixels
+};
+
+__device__ __forceinline__ void p2_locate(u64 q, u32 W, u32 &y, u32 &x)
+{
+    y = (u32)(q / W);
+    x = (u32)(q - (u64)y * W);
+}
+
+__device__ __forceinline__ void p2_load(const ImgDesc &d, const uint8_t *fsrc, long long fpitch, u64 q, u32 y,
+                                        u32 x, u32 n, P2Group &g)
+{
+    const u32 W = (u32)d.W;
+    const float2 *pp = reinterpret_cast<const float2 *>(d.plane) + q;
+    const uint8_t *fp = fsrc + (long long)y * fpitch + (long long)x * d.elem;
+    const uintptr_t fa = reinterpret_cast<uintptr_t>(fp);
+    if (n == 4 && x + 4u <= W && (d.elem == 1 ? (fa & 3) == 0 : (fa & 7) == 0)) {
+        g.a = __ldcg(reinterpret_cast<const float4 *>(pp));
+        g.b = __ldcg(reinterpret_cast<const float4 *>(pp) + 1);
+        if (d.elem == 1) {
+            const u32 v = __ldcg(reinterpret_cast<const unsigned int *>(fp));
+            g.f[0] = v & 0xffu;
+            g.f[1] = (v >> 8) & 0xffu;
+            g.f[2] = (v >> 16) & 0xffu;
+            g.f[3] = v >> 24;
+        } else {
+            const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(fp));
+            g.f[0] = v.x & 0xffffu;
+            g.f[1] = v.x >> 16;
+            g.f[2] = v.y & 0xffffu;
+            g.f[3] = v.y >> 16;
+        }
+        return;
+    }
+    float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    u32 yy = y, xx = x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        g.f[i] = 0;
+        if ((u32)i < n) {
+            const float2 v = __ldcg(pp + i);
+            m[2 * i] = v.x;
+            m[2 * i + 1] = v.y;
+            const uint8_t *p = fsrc + (long long)yy * fpitch + (long long)xx * d.elem;
+            g.f[i] = d.elem == 1 ? (u32)__ldcg(p) : (u32)__ldcg(reinterpret_cast<const u16 *>(p));
+            if (++xx == W) {
+                xx = 0;
+                ++yy;
+            }
+        }
+    }
+    g.a = make_float4(m[0], m[1], m[2], m[3]);
+    g.b = make_float4(m[4], m[5], m[6], m[7]);
+}
+
+__device__ __forceinline__ void p2_store(const ImgDesc &d, u64 q, u32 y, u32 x, u32 n, const P2Group &g,
+                                         const ApplyConst &k)
+{
+    const u32 W = (u32)d.W;
+    u32 o[4];
+    float yv[4];
+    o[0] = wiener_ms(g.a.x, g.a.y, g.f[0], k, yv[0]);
+    o[1] = wiener_ms(g.a.z, g.a.w, g.f[1], k, yv[1]);
+    o[2] = wiener_ms(g.b.x, g.b.y, g.f[2], k, yv[2]);
+    o[3] = wiener_ms(g.b.z, g.b.w, g.f[3], k, yv[3]);
+    uint8_t *op = d.dst + (long long)y * d.dst_pitch + (long long)x * d.elem;
+    const uintptr_t oa = reinterpret_cast<uintptr_t>(op);
+    if (n == 4 && x + 4u <= W && d.elem == 1 && (oa & 3) == 0) {
+        *reinterpret_cast<u32 *>(op) = o[0] | (o[1] << 8) | (o[2] << 16) | (o[3] << 24);
+    } else if (n == 4 && x + 4u <= W && d.elem == 2 && (oa & 7) == 0) {
+        *reinterpret_cast<uint2 *>(op) = make_uint2(o[0] | (o[1] << 16), o[2] | (o[3] << 16));
+    } else {
+        u32 yy = y, xx = x;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if ((u32)i < n) {
+                uint8_t *p = d.dst + (long long)yy * d.dst_pitch + (long long)xx * d.elem;
+                if (d.elem == 1) *p = (uint8_t)o[i];
+                else *reinterpret_cast<u16 *>(p) = (u16)o[i];
+                if (++xx == W) {
+                    xx = 0;
+                    ++yy;
+                }
+            }
+        }
+    }
+    if (d.y_out) {
+        float *yp = d.y_out + q;
+        if (n == 4 && (reinterpret_cast<uintptr_t>(yp) & 15) == 0) {
+            *reinterpret_cast<float4 *>(yp) = make_float4(yv[0], yv[1], yv[2], yv[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((u32)i < n) yp[i] = yv[i];
+        }
+    }
+}
+
+__device__ void p2_direct(const ImgDesc &d, const LaunchParams &lp, BlockShared &bs)
+{
+    HD_STAMP_INIT();
+    if (!wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag)) return;
+    HD_STAMP(12);
+    const u64 P0 = (u64)d.own0 * (u64)d.W, NP = (u64)(d.own1 - d.own0) * (u64)d.W;
+    const u64 per = ((NP + 1) / 2 + gridDim.x - 1) / gridDim.x;     // pixel pairs per CTA
+    const u64 pb = P0 + min(NP, 2 * per * blockIdx.x), pe = P0 + min(NP, 2 * per * (blockIdx.x + 1));
+    const bool hyb = d.mode == MODE_HYBRID_EST;
+    const uint8_t *fsrc = hyb ? d.fbuf : d.src;
+    const long long fpitch = hyb ? d.f_pitch : d.src_pitch;
+    const u32 W = (u32)d.W;
+    constexpr u32 kStep = 4u * kThreads;
+    // the first group's loads go out while thread 0 converts the noise variance
+    u64 q = pb + 4u * threadIdx.x;
+    u32 y = 0, x = 0;
+    P2Group cur;
+    if (q < pe) {
+        p2_locate(q, W, y, x);
+        p2_load(d, fsrc, fpitch, q, y, x, (u32)min((u64)4, pe - q), cur);
+    }
+    if (threadIdx.x == 0) {
+        const double nu2 = noise_variance(d.ctl, (u64)d.w * (u64)d.wh, d.Hg, d.W, d.inv_den);
+        bs.nu2 = nu2;
+        bs.nu2f = __double2float_rn(nu2);
+        if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
+    }
+    __syncthreads();
+    HD_STAMP(21);
+    ApplyConst k;
+    k.n = 0;
+    k.v2f = bs.nu2f;
+    k.inv_n = 0.f;
+    k.inv_n2 = 0.f;
+    k.maxv = (u32)d.maxv;
+    while (q < pe) {
+        const u32 n = (u32)min((u64)4, pe - q);
+        const u64 qn = q + kStep;
+        u32 yn = y, xn = x + kStep;
+        while (xn >= W) {
+            xn -= W;
+            ++yn;
+        }
+        P2Group nxt;
+        if (qn < pe) p2_load(d, fsrc, fpitch, qn, yn, xn, (u32)min((u64)4, pe - qn), nxt);
+        p2_store(d, q, y, x, n, cur, k);
+        cur = nxt;
+        q = qn;
+        y = yn;
+        x = xn;
+    }
+    HD_STAMP(20);
+}
+
 // Plane-mode phase 2 of the CTA's share of image d: pixels [pb, pe), the
 // gridDim.x shares being equal up to a pixel pair.
 __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &vw, BlockShared &bs)
 {
+    HD_STAMP_INIT();
     if (!wait_phase1(d, (u32)(d.tiles_x * d.tiles_y), lp.spin_limit, &bs.flag)) return;
+    HD_STAMP(12);
+    HD_CTA_T(2);
     // the plane and f rows were written by other CTAs (generic stores, made
     // visible by the wait); the bulk copies read them through the async proxy
     if (threadIdx.x < kStages) asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1744,10 +1930,13 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
         if (blockIdx.x == 0 && d.noise_var_out) *d.noise_var_out = nu2;
     }
     __syncthreads();
+    HD_STAMP(21);
     for (int k = 0; k < K; ++k) {
         const int st = k % kStages;
         const bool late = !mbar_wait(&bs.full[st], (bs.fullpar >> st) & 1u, lp.spin_limit);
+        HD_STAMP(19);
         p2_apply(d, vw.stage + (size_t)st * kStageBytes, bs.st[st], bs.nu2f);
+        HD_STAMP(20);
         if (__syncthreads_or(late)) {
             // a copy did not land in time: report, wait (bounded) for the
             // copies still in flight, and give up the share
@@ -1775,7 +1964,9 @@ __device__ void p2_share(const ImgDesc &d, const LaunchParams &lp, const Views &
                 bs.st[st].n = 0;
             }
         }
+        HD_STAMP(22);
     }
+    HD_STAMP(13);
 }
 
 __device__ __forceinline__ bool image_narrow(const ImgDesc &d)
@@ -1836,6 +2027,11 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
     vw.h2 = smem_raw + L.h2;
 
     const Seg *segs = lp.segs ? lp.segs : lp.oneseg;
+    HD_STAMP_INIT();
+    HD_CTA_T(0);
+#ifdef HD_STAGE_PROFILE
+    int nitems = 0;
+#endif
     int buf = 0;
     int item;
     if (threadIdx.x == 0) {
@@ -1862,6 +2058,9 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         int next = 0;
         if (lp.ticket && threadIdx.x == 0) next = (int)atomicAdd(lp.ticket, 1u);
         run_item(d, sg.phase, item - sg.first, lp, vw, bs);
+#ifdef HD_STAGE_PROFILE
+        ++nitems;
+#endif
         if (lp.ticket && threadIdx.x == 0) bs.item[buf ^ 1] = next;
         __syncthreads();
         if (lp.ticket) {
@@ -1871,8 +2070,15 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
             item += gridDim.x;
         }
     }
+    HD_STAMP(14);
+    HD_CTA_T(1);
+    HD_CTA_ITEMS(nitems);
     // plane mode: every CTA applies its share of the image's phase 2
-    if (lp.p2_plane) p2_share(lp.one, lp, vw, bs);
+    if (lp.p2_plane) {
+        if (lp.p2_direct) p2_direct(lp.one, lp, bs);
+        else p2_share(lp.one, lp, vw, bs);
+    }
+    HD_CTA_T(3);
     // The last CTA out leaves the queue counters and control blocks zeroed
     // for the next launch on this workspace.
     if (lp.ticket && threadIdx.x == 0) {
@@ -1987,11 +2193,16 @@ int sm_count()
 }
 
 #ifdef HD_STAGE_PROFILE
+extern "C" int hd_debug_cta_times(unsigned long long *out, int n)
+{
+    return (int)cudaMemcpyFromSymbol(out, g_cta_t, (size_t)n * 5 * sizeof(unsigned long long));
+}
+
 extern "C" int hd_debug_stage_cycles(unsigned long long *out16, int clear)
 {
-    cudaError_t e = cudaMemcpyFromSymbol(out16, g_stage_cycles, 16 * sizeof(unsigned long long));
+    cudaError_t e = cudaMemcpyFromSymbol(out16, g_stage_cycles, 32 * sizeof(unsigned long long));
     if (e == cudaSuccess && clear) {
-        unsigned long long z[16] = {0};
+        unsigned long long z[32] = {0};
         e = cudaMemcpyToSymbol(g_stage_cycles, z, sizeof(z));
     }
     return (int)e;

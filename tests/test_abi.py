@@ -126,7 +126,7 @@ def test_workspace_sizes():
 def test_tuning_validation():
     old = hd.hd_get_tuning()
     try:
-        for bad in ((8, 0), (20, 0), (136, 0), (32, 9), (32, -1), (32, 0, 2), (32, 0, -1), (32, 0, 0, 33),
+        for bad in ((8, 0), (20, 0), (136, 0), (32, 9), (32, -1), (32, 0, 4), (32, 0, -1), (32, 0, 0, 33),
                     (32, 0, 0, -2), (32, 0, 0, 0, 3), (32, 0, 0, 0, 16), (32, 0, 0, 0, 0, 65), (32, 0, 0, 0, 0, -1),
                     (32, 0, 0, 0, 0, 0, 2)):
             with pytest.raises(hd.HDError):
@@ -135,6 +135,9 @@ def test_tuning_validation():
         assert hd.hd_get_tuning() == (64, 2, 0, 0, 0, 0, 0)
         hd.hd_set_tuning(48, 3, 1, -1, 8, 5, 1)
         assert hd.hd_get_tuning() == (48, 3, 1, -1, 8, 5, 1)
+        for plane in (2, 3):        # the plane with its Wiener pass staged / read from L2
+            hd.hd_set_tuning(32, 0, plane)
+            assert hd.hd_get_tuning()[2] == plane
     finally:
         hd.hd_set_tuning(*old)
 

@@ -220,6 +220,48 @@ def test_recompute_path_matches_oracle(shape, dtype, bits):
             check_wiener(out, nu2, y, ref_w, bits)
 
 
+@pytest.mark.parametrize("plane", [2, 3])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (31, 33), (33, 65), (130, 257), (257, 130)])
+@pytest.mark.parametrize("dtype,bits", [(np.uint8, 8), (np.uint16, 12)])
+def test_plane_pass_staged_and_direct_match_oracle(plane, shape, dtype, bits):
+    """The Wiener pass from the statistics plane, forced to stage it in shared
+    memory (plane knob 2) or to read it straight from L2 (3), on ragged shapes,
+    pitched buffers, both borders, with the binary32 value."""
+    g = noisy_image(*shape, dtype, seed=11 * shape[0] + shape[1] + plane)
+    old = hd.hd_get_tuning()
+    try:
+        hd.hd_set_tuning(old[0], old[1], plane, *old[3:])
+        for smax, w, pad in ((3, 3, 0), (7, 5, 5), (11, 7, 1)):
+            for border in (0, 1):
+                f, ref = oracle.hybrid(g, smax, w, bits=bits, border_zero=bool(border))
+                out, nu2, y = gpu_hybrid(g, smax, w, border=border, bits=bits, pad=pad, want_y=True)
+                check_wiener(out, nu2, y, ref, bits)
+                ref_w = oracle.wiener(f, w, noise_var=-1.0, bits=bits, border_zero=bool(border))
+                out, nu2, y = gpu_wiener(f, w, border=border, bits=bits, pad=pad)
+                check_wiener(out, nu2, y, ref_w, bits)
+    finally:
+        hd.hd_set_tuning(*old)
+
+
+def test_plane_pass_staged_direct_and_recompute_identical():
+    """paper1620 (the plane's working set fits L2: read straight from it by
+    default) through all three Wiener passes."""
+    spec, clean, g = synth.config_image("paper1620")
+    old = hd.hd_get_tuning()
+    try:
+        outs = []
+        for plane in (2, 3):
+            hd.hd_set_tuning(old[0], old[1], plane, *old[3:])
+            outs.append(gpu_hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits, want_y=True))
+    finally:
+        hd.hd_set_tuning(*old)
+    outs.append(gpu_hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits, want_y=True, minimal=True))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0][0], o[0])
+        assert outs[0][1] == o[1]
+        np.testing.assert_array_equal(outs[0][2], o[2])
+
+
 def test_plane_and_recompute_paths_identical():
     spec, clean, g = synth.config_image("paper1620")
     a = gpu_hybrid(g, spec.smax, spec.wiener_w, bits=spec.bits, want_y=True)
