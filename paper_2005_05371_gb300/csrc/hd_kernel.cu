@@ -94,6 +94,8 @@ __device__ __forceinline__ unsigned long long hd_gtime()
     do {                                                                             \
         if (threadIdx.x == 0 && blockIdx.x < 4096) g_cta_t[blockIdx.x][i] = hd_gtime(); \
     } while (0)
+// Clock cycles of each phase-1 item, by tile index (single images).
+__device__ unsigned int g_tile_cyc[1 << 16];
 #define HD_CTA_ITEMS(n)                                                              \
     do {                                                                             \
         if (threadIdx.x == 0 && blockIdx.x < 4096) g_cta_t[blockIdx.x][4] = (n);    \
@@ -404,7 +406,7 @@ __device__ __forceinline__ void wl_append(bool flo, bool fhi, int r, int lane, u
 __device__ void amf3_packed(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl, int *cnt, int FH)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int RS = FH / kWarps;
+    const int RS = (g.nrow + kWarps - 1) / kWarps;     // rows per warp
     const int r0 = warp * RS, r1 = min(r0 + RS, g.nrow);
     if (r0 >= r1) return;
     const bool on_lo = 2 * lane < g.ncol, on_hi = 2 * lane + 1 < g.ncol;
@@ -462,7 +464,7 @@ __device__ void amf3_packed(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *
 __device__ void amf3_scalar(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *fs, u16 *wl, int *cnt, int FH)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int RS = FH / kWarps;
+    const int RS = (g.nrow + kWarps - 1) / kWarps;     // rows per warp
     const int r0 = warp * RS, r1 = min(r0 + RS, g.nrow);
     if (r0 >= r1) return;
     const bool smax3 = d.smax == 3, keep = d.unresolved != 0;
@@ -2005,9 +2007,15 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
     }
     const bool pack = d.maxv < 0x8000;
     const bool narrow = image_narrow(d);
+#ifdef HD_STAGE_PROFILE
+    const long long tc0 = clock64();
+#endif
     if (pack && narrow) run_item_t<true, true>(d, phase, g, lp, vw, bs);
     else if (pack) run_item_t<true, false>(d, phase, g, lp, vw, bs);
     else run_item_t<false, false>(d, phase, g, lp, vw, bs);
+#ifdef HD_STAGE_PROFILE
+    if (threadIdx.x == 0 && phase == 1 && tile < (1 << 16)) g_tile_cyc[tile] = (unsigned int)(clock64() - tc0);
+#endif
 }
 
 __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid_constant__ LaunchParams lp)
@@ -2193,6 +2201,11 @@ int sm_count()
 }
 
 #ifdef HD_STAGE_PROFILE
+extern "C" int hd_debug_tile_cycles(unsigned int *out, int n)
+{
+    return (int)cudaMemcpyFromSymbol(out, g_tile_cyc, (size_t)n * sizeof(unsigned int));
+}
+
 extern "C" int hd_debug_cta_times(unsigned long long *out, int n)
 {
     return (int)cudaMemcpyFromSymbol(out, g_cta_t, (size_t)n * 5 * sizeof(unsigned long long));
