@@ -239,7 +239,7 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
     const int xa = max(gx0, 0), xb = min(gx0 + cols, W);   // in-image columns, xa < xb
     const int J = ((xb - xa) * es + 15) / 16 + 1;          // blocks that can hold a row's bytes
     const int jobs = rows * J;
-    constexpr int U = 2;
+    constexpr int U = 1;      // one block a pass (more unrolling measured slower: code size)
     for (int j0 = threadIdx.x; j0 < jobs; j0 += kThreads * U) {
         uint4 v[U];
         int lo[U], hi[U], row[U];
@@ -430,7 +430,7 @@ __device__ void amf3_packed(const ImgDesc &d, const Geo &g, const u16 *gs, u16 *
     u32 pl, pm, ph, pc, cl, cm, ch, cc;
     rowsort(r0 - 1, pl, pm, ph, pc);
     rowsort(r0, cl, cm, ch, cc);
-#pragma unroll 4
+#pragma unroll 2
     for (int r = r0; r < r1; ++r) {
         u32 nl, nm, nh, nc;
         rowsort(r + 1, nl, nm, nh, nc);
@@ -610,13 +610,13 @@ __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur,
             } else {
                 const u16 *top = ctr - R * g.GS, *bot = ctr + R * g.GS;
                 u32 rmin = 0xffffu, rmax = 0u;
-#pragma unroll 4
+#pragma unroll 2
                 for (int dx = -R; dx <= R; ++dx) {
                     const u32 a = top[dx], b = bot[dx];
                     rmin = umin(rmin, umin(a, b));
                     rmax = umax(rmax, umax(a, b));
                 }
-#pragma unroll 4
+#pragma unroll 2
                 for (int dy = 1 - R; dy < R; ++dy) {
                     const u32 a = ctr[dy * g.GS - R], b = ctr[dy * g.GS + R];
                     rmin = umin(rmin, umin(a, b));
@@ -628,13 +628,13 @@ __device__ void grow_level(const Geo &g, const u16 *gs, u16 *fs, const u16 *cur,
                 zmax = umax(pmax, rmax);
                 cmin = zmin == pmin ? (cc & 0xffu) : 0u;
                 cmax = zmax == pmax ? (cc >> 8) : 0u;
-#pragma unroll 4
+#pragma unroll 2
                 for (int dx = -R; dx <= R; ++dx) {
                     const u32 a = top[dx], b = bot[dx];
                     cmin += (a == zmin) + (b == zmin);
                     cmax += (a == zmax) + (b == zmax);
                 }
-#pragma unroll 4
+#pragma unroll 2
                 for (int dy = 1 - R; dy < R; ++dy) {
                     const u32 a = ctr[dy * g.GS - R], b = ctr[dy * g.GS + R];
                     cmin += (a == zmin) + (b == zmin);
@@ -1646,9 +1646,12 @@ __device__ __forceinline__ void tile_shape(int rw, int ry, int FH, int &Lm, int 
     TH = FH - 2 * ry;
 }
 
-template <bool PACK, bool NARROW>
+// One work item.  Only the Wiener sums depend on `narrow` (32-bit sums exact):
+// the median stages exist once per PACK, so a batch with both kinds of
+// images does not run two copies of them (the instruction cache is a limit).
+template <bool PACK>
 __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const LaunchParams &lp, const Views &vw,
-                           BlockShared &bs)
+                           BlockShared &bs, bool narrow)
 {
     const int mode = d.mode;
     const int FH = lp.region_h;
@@ -1705,8 +1708,13 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         HD_STAMP(3);
     }
     if (phase == 1 && est) {
-        if (d.plane) tile_stats<NARROW, true>(d, g, vw.fs, vw.h1, vw.h2, bs);
-        else tile_stats<NARROW, false>(d, g, vw.fs, vw.h1, vw.h2, bs);
+        if (PACK && narrow) {
+            if (d.plane) tile_stats<true, true>(d, g, vw.fs, vw.h1, vw.h2, bs);
+            else tile_stats<true, false>(d, g, vw.fs, vw.h1, vw.h2, bs);
+        } else {
+            if (d.plane) tile_stats<false, true>(d, g, vw.fs, vw.h1, vw.h2, bs);
+            else tile_stats<false, false>(d, g, vw.fs, vw.h1, vw.h2, bs);
+        }
         HD_STAMP(4);
         return;
     }
@@ -1723,7 +1731,8 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         if (g.x0 == 0 && g.y0 == 0 && d.noise_var_out) *d.noise_var_out = bs.nu2;
     }
     __syncthreads();
-    tile_apply<NARROW>(d, g, vw.fs, vw.h1, vw.h2, bs.nu2f);
+    if (PACK && narrow) tile_apply<true>(d, g, vw.fs, vw.h1, vw.h2, bs.nu2f);
+    else tile_apply<false>(d, g, vw.fs, vw.h1, vw.h2, bs.nu2f);
     HD_STAMP(6);
 }
 
@@ -2010,9 +2019,8 @@ __device__ void run_item(const ImgDesc &d, int phase, int tile, const LaunchPara
 #ifdef HD_STAGE_PROFILE
     const long long tc0 = clock64();
 #endif
-    if (pack && narrow) run_item_t<true, true>(d, phase, g, lp, vw, bs);
-    else if (pack) run_item_t<true, false>(d, phase, g, lp, vw, bs);
-    else run_item_t<false, false>(d, phase, g, lp, vw, bs);
+    if (pack) run_item_t<true>(d, phase, g, lp, vw, bs, narrow);
+    else run_item_t<false>(d, phase, g, lp, vw, bs, false);
 #ifdef HD_STAGE_PROFILE
     if (threadIdx.x == 0 && phase == 1 && tile < (1 << 16)) g_tile_cyc[tile] = (unsigned int)(clock64() - tc0);
 #endif
