@@ -186,17 +186,17 @@ __device__ __forceinline__ u32 vmed3(u32 a, u32 b, u32 c) { return vmax(vmin(a, 
 __device__ __forceinline__ u32 smed3(u32 a, u32 b, u32 c) { return umax(umin(a, b), umin(umax(a, b), c)); }
 
 // ---------------------------------------------------------------- region loads / stores
-template <bool CG, typename T>
-__device__ __forceinline__ T ldg_any(const T *p)
+// cg: through L2 only (data written earlier in this launch by other CTAs);
+// otherwise the read-only path.  A runtime flag: one copy of the load code.
+template <typename T>
+__device__ __forceinline__ T ldg_any(const T *p, bool cg)
 {
-    if (CG) return __ldcg(p);
-    return __ldg(p);
+    return cg ? __ldcg(p) : __ldg(p);
 }
 
 // Bytes [lo, hi) of the aligned 16-byte block at blk, by aligned pieces, into
 // q0 (bytes 0..7) and q1 (bytes 8..15); nothing outside [lo, hi) is read.
-template <bool CG>
-__device__ __noinline__ void load_partial(const uint8_t *blk, int lo, int hi, u64 &q0, u64 &q1)
+__device__ __noinline__ void load_partial(const uint8_t *blk, int lo, int hi, u64 &q0, u64 &q1, bool cg)
 {
     q0 = 0;
     q1 = 0;
@@ -204,16 +204,16 @@ __device__ __noinline__ void load_partial(const uint8_t *blk, int lo, int hi, u6
         u64 v;
         int s;
         if ((lo & 7) == 0 && lo + 8 <= hi) {
-            v = ldg_any<CG>(reinterpret_cast<const unsigned long long *>(blk + lo));
+            v = ldg_any(reinterpret_cast<const unsigned long long *>(blk + lo), cg);
             s = 8;
         } else if ((lo & 3) == 0 && lo + 4 <= hi) {
-            v = ldg_any<CG>(reinterpret_cast<const unsigned int *>(blk + lo));
+            v = ldg_any(reinterpret_cast<const unsigned int *>(blk + lo), cg);
             s = 4;
         } else if ((lo & 1) == 0 && lo + 2 <= hi) {
-            v = ldg_any<CG>(reinterpret_cast<const unsigned short *>(blk + lo));
+            v = ldg_any(reinterpret_cast<const unsigned short *>(blk + lo), cg);
             s = 2;
         } else {
-            v = ldg_any<CG>(blk + lo);
+            v = ldg_any(blk + lo, cg);
             s = 1;
         }
         if (lo < 8) q0 |= v << (8 * lo);
@@ -232,9 +232,8 @@ __device__ __noinline__ void load_partial(const uint8_t *blk, int lo, int hi, u6
 // at the buffer's two ends are aligned narrower pieces used.  Whole blocks
 // whose first pixel lands on a 4-byte aligned shared address go to shared
 // memory as 32-bit pixel pairs.
-template <bool CG>
 __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t *base, long long pitch, int es,
-                            int H, int W, int gy0, int gx0, bool zero_outside, const uint8_t *buf_hi)
+                            int H, int W, int gy0, int gx0, bool zero_outside, const uint8_t *buf_hi, bool cg)
 {
     const int xa = max(gx0, 0), xb = min(gx0 + cols, W);   // in-image columns, xa < xb
     const int J = ((xb - xa) * es + 15) / 16 + 1;          // blocks that can hold a row's bytes
@@ -267,10 +266,10 @@ __device__ void load_region(u16 *dst, int ds, int rows, int cols, const uint8_t 
                 hi[u] = blk + 16 > b ? (int)(b - blk) : 16;
                 xblk[u] = (long long)(blk - rp);    // byte offset of the block within the row
                 if (blk >= base && blk + 16 <= buf_hi) {
-                    v[u] = ldg_any<CG>(reinterpret_cast<const uint4 *>(blk));
+                    v[u] = ldg_any(reinterpret_cast<const uint4 *>(blk), cg);
                 } else {
                     u64 q0, q1;
-                    load_partial<CG>(blk, lo[u], hi[u], q0, q1);
+                    load_partial(blk, lo[u], hi[u], q0, q1, cg);
                     v[u] = make_uint4((u32)q0, (u32)(q0 >> 32), (u32)q1, (u32)(q1 >> 32));
                 }
             }
@@ -1171,7 +1170,7 @@ __device__ void tile_stats(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H
     const int w = d.w, wy = d.wh;      // window columns, rows
     constexpr bool with_plane = PLANE;
     HD_STAMP_INIT();
-    hsums<NARROW>(g, fs, H1, h2p, w, with_plane);
+    // H1 (and H2 with a plane) are in place: run_item_t ran hsums
     const bool zero = d.border_zero != 0;
     const int gy0 = g.y0 + d.gy_off;       // the tile's first row in the whole image
     const bool interior = !zero && gy0 >= g.Ry && gy0 + g.th <= d.Hg - g.Ry && g.x0 >= g.Rw &&
@@ -1526,8 +1525,7 @@ template <bool NARROW>
 __device__ void tile_apply(const ImgDesc &d, const Geo &g, const u16 *fs, u32 *H1, void *h2p, float v2f)
 {
     const int w = d.w, wy = d.wh;      // window columns, rows
-    hsums<NARROW>(g, fs, H1, h2p, w, true);
-    __syncthreads();
+    // H1 and H2 are in place (run_item_t ran hsums, then a block barrier)
     ApplyConst k;
     k.n = (u32)(w * wy);
     k.v2f = v2f;
@@ -1660,13 +1658,22 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
 
     const bool est = mode == MODE_HYBRID_EST || mode == MODE_WIENER_EST;
 
-    // ---- the f region in shared memory
-    if (do_amf) {
-        if (threadIdx.x == 0) bs.cnt[0] = 0;
-        load_region<false>(vw.gs + g.pa, g.GS, g.nrow + 2 * g.Ra, g.ncol + 2 * g.Ra, d.src, d.src_pitch, d.elem,
-                           d.H, d.W, g.gfy - g.Ra, g.gfx - g.Ra, false,
-                           d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem);
+    // ---- the region in shared memory, by one call site (one copy of the load
+    // code): the noisy input with the median halo, or the f region (from the
+    // median plane in a phase-2 item, else the input)
+    {
+        const bool fpl = !do_amf && phase == 2 && mode == MODE_HYBRID_EST;
+        const uint8_t *base = fpl ? d.fbuf : d.src;
+        const long long pitch = fpl ? d.f_pitch : d.src_pitch;
+        const uint8_t *hi = fpl ? d.fbuf + (long long)d.H * d.f_pitch
+                                : d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem;
+        const int ra = do_amf ? g.Ra : 0;
+        if (do_amf && threadIdx.x == 0) bs.cnt[0] = 0;
+        load_region(do_amf ? vw.gs + g.pa : vw.fs, do_amf ? g.GS : FS, g.nrow + 2 * ra, g.ncol + 2 * ra, base, pitch,
+                    d.elem, d.H, d.W, g.gfy - ra, g.gfx - ra, !do_amf && d.border_zero != 0, hi, fpl);
         __syncthreads();
+    }
+    if (do_amf) {
         HD_STAMP(0);
         if (PACK) amf3_packed(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
         else amf3_scalar(d, g, vw.gs, vw.fs, vw.wl0, &bs.cnt[0], FH);
@@ -1687,25 +1694,24 @@ __device__ void run_item_t(const ImgDesc &d, int phase, const Geo &g, const Laun
         }
         __syncthreads();
     } else {
-        if (phase == 2 && mode == MODE_HYBRID_EST)
-            load_region<true>(vw.fs, FS, g.nrow, g.ncol, d.fbuf, d.f_pitch, d.elem, d.H, d.W, g.gfy, g.gfx,
-                              d.border_zero != 0, d.fbuf + (long long)d.H * d.f_pitch);
-        else
-            load_region<false>(vw.fs, FS, g.nrow, g.ncol, d.src, d.src_pitch, d.elem, d.H, d.W, g.gfy, g.gfx,
-                               d.border_zero != 0,
-                               d.src + (long long)(d.H - 1) * d.src_pitch + (long long)d.W * d.elem);
-        __syncthreads();
         HD_STAMP(5);
     }
     if (do_amf) HD_STAMP(2);
 
-    if (mode == MODE_AMF) {
-        store_region(vw.fs, FS, g.th, g.tw, d.dst, d.dst_pitch, d.elem, g.y0, g.x0);
-        return;
-    }
-    if (phase == 1 && mode == MODE_HYBRID_EST) {
-        store_region(vw.fs + g.Ry * FS + g.Lm, FS, g.th, g.tw, d.fbuf, d.f_pitch, d.elem, g.y0, g.x0);
+    // the median output: the result (median only) or the median plane (one call site)
+    const bool amf_only = mode == MODE_AMF;
+    if (amf_only || (phase == 1 && mode == MODE_HYBRID_EST)) {
+        store_region(vw.fs + g.Ry * FS + g.Lm, FS, g.th, g.tw, amf_only ? d.dst : d.fbuf,
+                     amf_only ? d.dst_pitch : d.f_pitch, d.elem, g.y0, g.x0);
+        if (amf_only) return;
         HD_STAMP(3);
+    }
+    // the horizontal window sums of the f region, by one call site per sum
+    // width (the statistics pass needs H2 only for the plane)
+    {
+        const bool with_h2 = !(phase == 1 && est) || d.plane != nullptr;
+        if (PACK && narrow) hsums<true>(g, vw.fs, vw.h1, vw.h2, d.w, with_h2);
+        else hsums<false>(g, vw.fs, vw.h1, vw.h2, d.w, with_h2);
     }
     if (phase == 1 && est) {
         if (PACK && narrow) {
