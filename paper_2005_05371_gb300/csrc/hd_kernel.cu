@@ -1140,6 +1140,8 @@ struct P2Stage {
 
 struct BlockShared {
     int item[2];      // current / next ticket (double buffer)
+    Seg seg[2];       //   its segment
+    ImgDesc desc[2];  //   its image's descriptor (batches; single images read the launch parameters)
     u64 full[kStages];        // plane-mode phase 2: stage s staged (bulk-copy bytes landed)
     P2Stage st[kStages];      //   what each stage holds
     u32 fullpar;              //   bit s: parity of the next phase to wait for on stage s
@@ -1620,15 +1622,33 @@ struct Views {
     void *h2;
 };
 
-__device__ __forceinline__ int find_segment(const Seg *segs, int nsegs, int item)
+// Warp 0: the segment of ticket `item` (the last one with first <= item;
+// the table is sorted by first) by a 32-way search, one ballot a round (two
+// rounds for up to 1024 segments), into bs.seg[slot]; for batches also the
+// image's descriptor, copied into bs.desc[slot].  Every thread of the CTA
+// then reads both from shared memory instead of chasing the tables in
+// global memory.
+__device__ void resolve_item(const LaunchParams &lp, const Seg *segs, int item, BlockShared &bs, int slot)
 {
-    int lo = 0, hi = nsegs - 1;
-    while (lo < hi) {   // last segment with first <= item
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].first <= item) lo = mid;
-        else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    int stride = 1;
+    while (stride * 32 < lp.nsegs) stride *= 32;
+    int lo = 0;        // invariant: segs[lo].first <= item
+    for (;;) {
+        const int idx = lo + lane * stride;
+        const bool le = idx < lp.nsegs && segs[idx].first <= item;
+        const u32 b = __ballot_sync(FULL, le);      // a prefix of the lanes, lane 0 included
+        lo += (31 - __clz(b)) * stride;
+        if (stride == 1) break;
+        stride >>= 5;
     }
-    return lo;
+    const Seg sg = segs[lo];
+    if (lane == 0) bs.seg[slot] = sg;
+    if (lp.descs) {
+        const u32 *src = reinterpret_cast<const u32 *>(lp.descs + sg.img);
+        u32 *dst = reinterpret_cast<u32 *>(&bs.desc[slot]);
+        for (int i = lane; i < (int)(sizeof(ImgDesc) / 4); i += 32) dst[i] = src[i];
+    }
 }
 
 __device__ __forceinline__ bool mode_median(int mode)
@@ -2062,35 +2082,39 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         for (int i = 0; i < kStages; ++i) mbar_init(&bs.full[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    if (lp.ticket) {
-        if (threadIdx.x == 0) bs.item[0] = (int)atomicAdd(lp.ticket, 1u);
-        __syncthreads();
-        item = bs.item[0];
-    } else {
-        item = blockIdx.x;
+    // the first item: its ticket, segment and descriptor, resolved by warp 0
+    if (threadIdx.x < 32) {
+        int first = 0;
+        if (threadIdx.x == 0) first = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : (int)blockIdx.x;
+        first = __shfl_sync(FULL, first, 0);
+        if (threadIdx.x == 0) bs.item[0] = first;
+        if (first < lp.total_items) resolve_item(lp, segs, first, bs, 0);
     }
+    __syncthreads();
+    item = bs.item[0];
     while (item < lp.total_items) {
-        const Seg sg = segs[find_segment(segs, lp.nsegs, item)];
-        const ImgDesc &d = lp.descs ? lp.descs[sg.img] : lp.one;
+        const Seg sg = bs.seg[buf];
+        const ImgDesc &d = lp.descs ? bs.desc[buf] : lp.one;
         // Take the next ticket now and read it after the item: its latency
         // hides behind the work.  Tickets only grow, and an item waits only on
         // earlier tickets, so the CTA holding the earliest unfinished ticket
         // is always working on it: holding a later one cannot deadlock.
         int next = 0;
-        if (lp.ticket && threadIdx.x == 0) next = (int)atomicAdd(lp.ticket, 1u);
+        if (threadIdx.x == 0) next = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : item + (int)gridDim.x;
         run_item(d, sg.phase, item - sg.first, lp, vw, bs);
 #ifdef HD_STAGE_PROFILE
         ++nitems;
 #endif
-        if (lp.ticket && threadIdx.x == 0) bs.item[buf ^ 1] = next;
-        __syncthreads();
-        if (lp.ticket) {
-            buf ^= 1;
-            item = bs.item[buf];
-        } else {
-            item += gridDim.x;
+        // warp 0 resolves the next item into the other slot (the current
+        // slot stays valid until the barrier)
+        if (threadIdx.x < 32) {
+            next = __shfl_sync(FULL, next, 0);
+            if (threadIdx.x == 0) bs.item[buf ^ 1] = next;
+            if (next < lp.total_items) resolve_item(lp, segs, next, bs, buf ^ 1);
         }
+        __syncthreads();
+        buf ^= 1;
+        item = bs.item[buf];
     }
     HD_STAMP(14);
     HD_CTA_T(1);
