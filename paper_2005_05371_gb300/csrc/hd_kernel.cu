@@ -2082,18 +2082,22 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         for (int i = 0; i < kStages; ++i) mbar_init(&bs.full[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // the first item: its ticket, segment and descriptor, resolved by warp 0
+    // the first item: its ticket and, with tables (batches), its segment and
+    // descriptor, resolved by warp 0; a single image has at most two
+    // segments in the launch parameters
+    const bool tables = lp.segs != nullptr;
     if (threadIdx.x < 32) {
         int first = 0;
         if (threadIdx.x == 0) first = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : (int)blockIdx.x;
         first = __shfl_sync(FULL, first, 0);
         if (threadIdx.x == 0) bs.item[0] = first;
-        if (first < lp.total_items) resolve_item(lp, segs, first, bs, 0);
+        if (tables && first < lp.total_items) resolve_item(lp, segs, first, bs, 0);
     }
     __syncthreads();
     item = bs.item[0];
     while (item < lp.total_items) {
-        const Seg sg = bs.seg[buf];
+        const Seg sg = tables ? bs.seg[buf]
+                              : (lp.nsegs > 1 && item >= lp.oneseg[1].first ? lp.oneseg[1] : lp.oneseg[0]);
         const ImgDesc &d = lp.descs ? bs.desc[buf] : lp.one;
         // Take the next ticket now and read it after the item: its latency
         // hides behind the work.  Tickets only grow, and an item waits only on
@@ -2110,7 +2114,7 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         if (threadIdx.x < 32) {
             next = __shfl_sync(FULL, next, 0);
             if (threadIdx.x == 0) bs.item[buf ^ 1] = next;
-            if (next < lp.total_items) resolve_item(lp, segs, next, bs, buf ^ 1);
+            if (tables && next < lp.total_items) resolve_item(lp, segs, next, bs, buf ^ 1);
         }
         __syncthreads();
         buf ^= 1;
