@@ -1622,7 +1622,7 @@ struct Views {
     void *h2;
 };
 
-// Warp 0: the segment of ticket `item` (the last one with first <= item;
+// One warp: the segment of ticket `item` (the last one with first <= item;
 // the table is sorted by first) by a 32-way search, one ballot a round (two
 // rounds for up to 1024 segments), into bs.seg[slot]; for batches also the
 // image's descriptor, copied into bs.desc[slot].  Every thread of the CTA
@@ -2083,14 +2083,17 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the first item: its ticket and, with tables (batches), its segment and
-    // descriptor, resolved by warp 0; a single image has at most two
-    // segments in the launch parameters
+    // descriptor, resolved by the last warp (thread 0 ends a median item with
+    // the sums' atomics and the release of its done count, so the two waits
+    // overlap); a single image has at most two segments in the launch
+    // parameters
     const bool tables = lp.segs != nullptr;
-    if (threadIdx.x < 32) {
+    const bool rwarp = (threadIdx.x >> 5) == kWarps - 1, rlead = threadIdx.x == kThreads - 32;
+    if (rwarp) {
         int first = 0;
-        if (threadIdx.x == 0) first = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : (int)blockIdx.x;
+        if (rlead) first = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : (int)blockIdx.x;
         first = __shfl_sync(FULL, first, 0);
-        if (threadIdx.x == 0) bs.item[0] = first;
+        if (rlead) bs.item[0] = first;
         if (tables && first < lp.total_items) resolve_item(lp, segs, first, bs, 0);
     }
     __syncthreads();
@@ -2104,16 +2107,16 @@ __global__ void __launch_bounds__(kThreads, 4) hd_persistent_kernel(const __grid
         // earlier tickets, so the CTA holding the earliest unfinished ticket
         // is always working on it: holding a later one cannot deadlock.
         int next = 0;
-        if (threadIdx.x == 0) next = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : item + (int)gridDim.x;
+        if (rlead) next = lp.ticket ? (int)atomicAdd(lp.ticket, 1u) : item + (int)gridDim.x;
         run_item(d, sg.phase, item - sg.first, lp, vw, bs);
 #ifdef HD_STAGE_PROFILE
         ++nitems;
 #endif
-        // warp 0 resolves the next item into the other slot (the current
-        // slot stays valid until the barrier)
-        if (threadIdx.x < 32) {
+        // the last warp resolves the next item into the other slot (the
+        // current slot stays valid until the barrier)
+        if (rwarp) {
             next = __shfl_sync(FULL, next, 0);
-            if (threadIdx.x == 0) bs.item[buf ^ 1] = next;
+            if (rlead) bs.item[buf ^ 1] = next;
             if (tables && next < lp.total_items) resolve_item(lp, segs, next, bs, buf ^ 1);
         }
         __syncthreads();
