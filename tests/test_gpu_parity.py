@@ -369,6 +369,38 @@ def test_batched_equals_single_and_oracle():
         np.testing.assert_array_equal(to_host(single, g.dtype), batched)
 
 
+def test_batch_of_many_small_images():
+    """600 images of 1..40 pixels a side with estimated noise variance: 1200
+    segments of tickets, so the kernel's 32-way segment search takes three
+    rounds; the images finish in a few tiles each, so many items of many
+    images are in flight at once."""
+    rng = np.random.default_rng(606)
+    items, hosts = [], []
+    for i in range(600):
+        H, W = int(rng.integers(1, 41)), int(rng.integers(1, 41))
+        dtype = np.uint8 if i % 2 == 0 else np.uint16
+        bits = 8 if dtype == np.uint8 else 12
+        g = noisy_image(H, W, dtype, seed=60600 + i, density=float(rng.uniform(0, 0.5)))
+        p = hd.Params(int(rng.choice([3, 5, 7])), int(rng.choice([1, 3, 5])), -1.0, int(rng.integers(0, 2)), 0,
+                      bits)
+        items.append((to_dev(g), empty_like_dev(g), p))
+        hosts.append(g)
+    hd.hybrid_denoise_batched(items)
+    assert hd.hd_get_device_error() == hd.HD_OK
+    for (src, dst, p), g in zip(items, hosts):
+        np.testing.assert_array_equal(to_host(dst, g.dtype), _oracle_of(g, p).out32)
+    plan = hd.BatchPlan(items)
+    try:
+        for _, dst, _ in items:
+            dst.fill_(3)
+        plan.launch()
+        assert hd.hd_get_device_error() == hd.HD_OK
+        for (src, dst, p), g in zip(items, hosts):
+            np.testing.assert_array_equal(to_host(dst, g.dtype), _oracle_of(g, p).out32)
+    finally:
+        plan.close()
+
+
 def test_batch_plan_graph_replay():
     items, hosts = _batch_items(10, seed=5)
     plan = hd.BatchPlan(items)
