@@ -430,7 +430,7 @@ hd_status hd_batch_pipeline_destroy(hd_batch_pipeline *pipeline);
  *   plane:        0 = a single image uses the statistics plane whenever its
  *                 workspace has room for it, its Wiener pass reading the
  *                 plane straight from L2 when the plane, the median output
- *                 and the output of the image fit in half of the L2, else
+ *                 and the output of the image fit in the L2, else
  *                 staging it in shared memory by bulk copies; 1 = never
  *                 (recompute pass); 2 = the plane, always staged; 3 = the
  *                 plane, always read straight from L2.

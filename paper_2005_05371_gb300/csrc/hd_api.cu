@@ -215,12 +215,13 @@ hd_status finish_params(LaunchParams &lp, const hd_tuning &t, int *grid, size_t 
     if (t.ctas_per_sm > 0) per_sm = std::min(per_sm, t.ctas_per_sm);
     // plane mode: every resident CTA takes a share of the phase-2 pixels,
     // read straight from L2 when the plane, f and the output of the owned rows
-    // fit in half of it (they were written moments before), else staged by
-    // bulk copies, which keep more bytes in flight from HBM
+    // fit in it (they were written moments before; measured faster up to a
+    // 101 MB working set, slower from 154 MB), else staged by bulk copies,
+    // which keep more bytes in flight from HBM
     if (lp.p2_plane) {
         const ImgDesc &d = lp.one;
         const size_t px = (size_t)(d.own1 - d.own0) * (size_t)d.W;
-        lp.p2_direct = t.plane == 3 || (t.plane != 2 && px * (8 + 2 * (size_t)d.elem) <= device_l2_bytes() / 2);
+        lp.p2_direct = t.plane == 3 || (t.plane != 2 && px * (8 + 2 * (size_t)d.elem) <= device_l2_bytes());
     }
     *grid = std::max(1, lp.p2_plane ? sms * per_sm : std::min(lp.total_items, sms * per_sm));
     return HD_OK;

@@ -99,7 +99,7 @@ struct LaunchParams {
     int p2_plane;             // 1: `one` has a statistics plane; after the queue every CTA applies
                               // its own 1/gridDim share of the image's pixels from it
     int p2_direct;            // with the plane: 1 reads it straight from L2 (the phase-2 working set
-                              // fits in half the L2), 0 stages it through shared memory by bulk copies
+                              // fits the L2), 0 stages it through shared memory by bulk copies
     int small_growth;         // growth by one warp without barriers when at most this many pixels
                               // of a region fail level A at 3x3 (0: never)
     int select_lanes;         // cap on the lanes sharing one median selection (0: per window size)
