@@ -189,11 +189,15 @@ class Server:
     """Continuous batching with admission by a device-memory budget."""
 
     def __init__(self, budget_bytes: int = 8 << 30, max_inflight: int = 3, max_batch: int = 128,
-                 device="cuda:0", backend=None):
+                 device="cuda:0", backend=None, max_round_px: int = 64 << 20):
         self.backend = backend if backend is not None else CudaBackend(device, max_inflight)
         self.arena = self.backend.arena(budget_bytes)
         self.max_inflight = max_inflight
         self.max_batch = max_batch
+        # a round holds at most this many pixels (at least one request): after
+        # a burst, the backlog drains in rounds of bounded length instead of
+        # one long round that every request in it waits for
+        self.max_round_px = max_round_px
         self.lock = threading.Condition()
         self.waiting: deque[Request] = deque()     # arrived, not admitted
         self.admitted: deque[Request] = deque()    # on device, not launched
@@ -271,12 +275,19 @@ class Server:
             self.peak_used = max(self.peak_used, self.arena.used)
 
     def _launch_round(self) -> bool:
-        """Launch admitted requests (up to max_batch) as one batched kernel.
+        """Launch admitted requests (up to max_batch, and up to max_round_px
+        pixels) as one batched kernel.
         A round of several needs a workspace gap in the arena (the round is
         halved until one fits).  A lone request, or the first request when no
         gap fits and no round is running to free one, runs alone in its own
         block.  Returns False when the round has to wait for space."""
         take = min(len(self.admitted), self.max_batch)
+        px = self.admitted[0].pixels
+        for i in range(1, take):
+            px += self.admitted[i].pixels
+            if px > self.max_round_px:
+                take = i
+                break
         lone = take == 1
         a_ws = None
         while take >= 2:

@@ -45,6 +45,7 @@ class _FakeBackend:
         self.rng = np.random.default_rng(seed)
         self.live = []          # (lo, hi, round id) of regions in flight
         self.launches = []
+        self.round_px = []      # pixels of each round, in launch order
         self.overlaps = 0
 
     def thread_init(self):
@@ -76,6 +77,7 @@ class _FakeBackend:
         ev = _FakeEvent(int(self.rng.integers(1, 6)))
         self.live += [(lo, hi, rid, ev) for lo, hi in regions]
         self.launches.append((len(reqs), own, si))
+        self.round_px.append(sum(r.pixels for r in reqs))
         return ev
 
 
@@ -112,6 +114,33 @@ def test_scheduler_finishes_every_request_in_a_fragmented_arena():
     assert st["solo_rounds"] > 0 and st["rounds"] < st["requests"]
     busy_streams = [si for _, _, si in fake.launches]
     assert set(busy_streams) <= {0, 1, 2}
+
+
+def test_rounds_hold_at_most_the_pixel_cap():
+    """After a burst, rounds take admitted requests in order up to the pixel
+    cap (a request larger than the cap runs alone), so no round holds the
+    whole backlog."""
+    ensure_built()
+    from paper_2005_05371_gb300 import Params
+    from paper_2005_05371_gb300.serve import Server
+    rng = np.random.default_rng(12)
+    fake = _FakeBackend(13)
+    cap = 300_000
+    srv = Server(budget_bytes=64 << 20, max_inflight=2, backend=fake, max_round_px=cap)
+    try:
+        sizes = [(int(rng.integers(50, 400)), int(rng.integers(50, 400))) for _ in range(200)]
+        sizes[7] = (700, 700)                       # larger than the cap alone
+        reqs = [srv.submit(np.zeros(hw, np.uint8), Params(5, 3, bits=8)) for hw in sizes]
+        for r in reqs:
+            assert r.done.wait(30), "a request never finished"
+    finally:
+        srv.close()
+    assert fake.overlaps == 0 and all(r.error is None for r in reqs)
+    assert sum(n for n, _, _ in fake.launches) == len(reqs)
+    for (n, _, _), px in zip(fake.launches, fake.round_px):
+        assert px <= cap or n == 1            # only a lone request may exceed the cap
+    assert any(n > 1 for n, _, _ in fake.launches)           # rounds still batch
+    assert 700 * 700 in fake.round_px                         # the large one ran alone
 
 
 gpu = pytest.mark.gpu
